@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test names the passage or the closed form it checks.  None retypes an oracle formula: the
+expected values come from the paper's printed numbers (tests/golden), closed-form solutions,
+brute force, invariants, or an independent integration of the density matrix.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import oracle_inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------------------------------------
+# FFT and random numbers
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 64, 256])
+def test_fft_matches_bruteforce_dft(oracle_lib, n):
+    o = oracle_lib
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for sign in (-1, 1):
+        X = o.fft(x, sign)
+        Xd = o.dft(x, sign)
+        # the DFT definition, also checked against the textbook formula written with numpy
+        jk = np.outer(np.arange(n), np.arange(n))
+        Xm = np.exp(sign * 2j * np.pi * jk / n) @ x
+        assert np.abs(Xd - Xm).max() <= 1e-12 * max(1.0, np.abs(Xm).max())
+        assert np.abs(X - Xd).max() <= 1e-13 * max(1.0, np.abs(Xd).max()) * max(1, np.log2(n))
+
+
+def test_fft_inverse_and_parseval(oracle_lib):
+    o = oracle_lib
+    rng = np.random.default_rng(3)
+    n = 4096
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    X = o.fft(x, -1)
+    assert abs(np.vdot(X, X).real / n - np.vdot(x, x).real) < 1e-12 * np.vdot(x, x).real
+    y = o.fft(X, +1) / n
+    assert np.abs(y - x).max() < 1e-13 * np.abs(x).max() * 12
+
+
+def test_philox_known_answers(oracle_lib):
+    for row in _read_golden("philox4x32_10_kat.txt"):
+        v = [int(t, 16) for t in row]
+        assert oracle_lib.philox4x32_10(v[0:4], v[4:6]) == tuple(v[6:10])
+
+
+def test_draws_uniform_in_open_interval(oracle_lib):
+    from scipy import stats
+    o = oracle_lib
+    d = np.array([o.draws(12345, k) for k in range(20000)])
+    assert (d > 0).all() and (d < 1).all()
+    for col in range(3):
+        assert stats.kstest(d[:, col], "uniform").pvalue > 1e-3
+    # different seeds give different streams, a given (seed, k) is reproducible
+    assert o.draws(1, 0) != o.draws(2, 0)
+    assert o.draws(7, 5) == o.draws(7, 5)
+
+
+# ------------------------------------------------------------------------------------------------
+# paper's printed constants
+# ------------------------------------------------------------------------------------------------
+def test_jump_matrix_matches_paper(oracle_lib):
+    """p(l -> l') of Eq. (pjump): the threshold of the oracle's rule on u_l in (0,1), found by
+    bisection, is the printed probability of jumping down."""
+    o = oracle_lib
+    M = np.array([[float(Fraction(t)) for t in row] for row in _read_golden("jump_matrix.txt")])
+    for l in range(4):
+        lo, hi = 0.0, 1.0
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if o.jump_l(l, mid) == l - 1:
+                lo = mid
+            else:
+                hi = mid
+        p_down = lo
+        if l - 1 >= 0:
+            assert abs(p_down - M[l - 1, l]) < 1e-12
+        else:
+            assert p_down == 0.0
+        if l + 1 < 4:
+            assert abs((1 - p_down) - M[l + 1, l]) < 1e-12
+        for lp in range(4):
+            if abs(lp - l) != 1:
+                assert M[lp, l] == 0.0
+    # empirical frequencies with the oracle's own draws, 2e5 samples, within 4 sigma
+    d = np.array([o.draws(99, k) for k in range(200000)])
+    for l in (1, 2, 3):
+        f = np.mean([o.jump_l(l, u) == l - 1 for u in d[:50000, 1]])
+        p = l / (2 * l + 1)
+        assert abs(f - p) < 4 * np.sqrt(p * (1 - p) / 50000)
+
+
+def test_colour_rule_and_potential_constants(oracle_lib):
+    o = oracle_lib
+    g = o.Grid()
+    consts = {k: float(Fraction(v)) for k, v in _read_golden("colour_and_potential_constants.txt")}
+    # colour thresholds by bisection on u_c
+    assert all(o.jump_color(g, 0, u) == 1 for u in np.linspace(1e-9, 1 - 1e-9, 101))
+    lo, hi = 0.0, 1.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if o.jump_color(g, 1, mid) == 0:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(lo - consts["p_o_to_s"]) < 1e-12
+    assert abs((1 - lo) - consts["p_o_to_o"]) < 1e-12
+    # potential: singlet -alpha/r, octet +alpha/(8 r), r^2 coefficients 1/2 and 7/32 (App. E)
+    alpha = consts["C_F"] * g.alpha_s
+    r = 0.7
+    vs = o.potential(g, 0, 0, 0.0, 0.0, 0.0, r)
+    vo = o.potential(g, 1, 0, 0.0, 0.0, 0.0, r)
+    assert abs(vs - (-alpha / r)) < 1e-15
+    assert abs(vo - consts["octet_coulomb_over_alpha"] * alpha / r) < 1e-15
+    T3, kap, gam = 0.07, 4.5, -1.3
+    for c, f in ((0, consts["singlet_r2_factor"]), (1, consts["octet_r2_factor"])):
+        dv = o.potential(g, c, 0, T3, kap, gam, r) - o.potential(g, c, 0, 0.0, 0.0, 0.0, r)
+        assert abs(dv.real - f * gam * T3 * r * r) < 1e-15
+        assert abs(dv.imag + f * kap * T3 * r * r) < 1e-15
+
+
+# ------------------------------------------------------------------------------------------------
+# split step: closed forms and invariants
+# ------------------------------------------------------------------------------------------------
+def _free_gaussian(r, D, t, M):
+    # free s-wave Gaussian u = r R of a particle of reduced mass M/2 (hbar = 1):
+    # R(r,t) = (D^2/a)^{3/2} exp(-r^2/(2a)),  a = D^2 + 2 i t / M
+    a = D * D + 2j * t / M
+    return D ** 3 * a ** -1.5 * r * np.exp(-r * r / (2 * a))
+
+
+@pytest.mark.parametrize("dt,steps", [(0.001, 2000), (0.05, 40)])
+def test_free_gaussian_spreading_closed_form(oracle_lib, dt, steps):
+    o = oracle_lib
+    g = o.Grid(N=512, L=20.0, dt=dt, alpha_s=0.0)
+    D = 0.5
+    r = np.arange(g.N) * (g.L / g.N)
+    u0 = _free_gaussian(r, D, 0.0, g.M).astype(np.complex128)
+    m = o.medium(kappa_hat=0.0, gamma_hat=0.0)
+    u, _ = o.evolve_nojump(g, u0, 0, 0, m, 0, steps)
+    ue = _free_gaussian(r, D, steps * dt, g.M)
+    assert np.linalg.norm(u - ue) / np.linalg.norm(ue) < 1e-10
+
+
+def test_derivtype1_matches_three_point_laplacian(oracle_lib):
+    """derivType 1 (Sec. 2.4): the kinetic operator is -(u_{j+1} - 2u_j + u_{j-1})/(M dr^2) with
+    Dirichlet walls; with V = 0 one step equals exp(-i dt H3) applied with a dense eigen-solver."""
+    o = oracle_lib
+    N, L, dt = 64, 8.0, 0.01
+    g = o.Grid(N=N, L=L, dt=dt, alpha_s=0.0, deriv_type=1)
+    dr = L / N
+    n = N - 1
+    H = (np.diag(np.full(n, 2.0)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)) / (g.M * dr * dr)
+    w, V = np.linalg.eigh(H)
+    rng = np.random.default_rng(0)
+    u0 = np.zeros(N, np.complex128)
+    u0[1:] = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    m = o.medium(kappa_hat=0.0, gamma_hat=0.0)
+    u, _ = o.evolve_nojump(g, u0, 0, 0, m, 0, 5)
+    ue = V @ (np.exp(-1j * w * 5 * dt) * (V.T @ u0[1:]))
+    assert np.abs(u[1:] - ue).max() < 1e-12 * np.abs(ue).max()
+    assert u[0] == 0
+
+
+def test_unitarity_for_real_potential(oracle_lib):
+    """kappa_hat = 0: Strang splitting of a real potential is unitary (Sec. 3.3); the discrete norm
+    stays 1 to rounding over the whole Bjorken profile (11,899 steps)."""
+    o = oracle_lib
+    g = o.Grid(N=512, L=20.0, dt=0.001)
+    m = o.medium(kappa_hat=0.0, gamma_hat=-2.0)
+    u0 = o.initial_state(g, o.init_spec())
+    assert abs(o.norm2(g, u0) - 1) < 1e-14
+    ns = o.n_steps(g, m)
+    assert ns == 11899
+    _, h = o.evolve_nojump(g, u0, 0, 0, m, 0, ns)
+    assert np.abs(h - 1).max() < 1e-12
+    _, h = o.evolve_nojump(g, u0, 1, 3, m, 0, 2000)   # octet, l = 3
+    assert np.abs(h - 1).max() < 1e-12
+
+
+def test_coulomb_energies_converge(oracle_lib):
+    """T = 0 Coulomb problem of reduced mass M/2: E_n = -M (C_F alpha_s)^2 / (4 n^2).  The energy is
+    read from the phase of <phi|psi(t)>.  The 1S error must fall under refinement of the grid at
+    fixed L (the analytic 1S has a kink in its odd extension, so convergence is algebraic); at the
+    finest grid the bounds below hold (1P pins the centrifugal term)."""
+    o = oracle_lib
+    M, alpha = 4.65, 4.0 / 3.0 * 0.3
+    t_steps = 5000
+    errs = {}
+    for N in (512, 2048):
+        g = o.Grid(N=N, L=20.0, dt=0.001)
+        m = o.medium(kappa_hat=0.0, gamma_hat=0.0)
+        dr = g.L / g.N
+        for (n, l) in ((1, 0), (2, 0), (2, 1)):
+            phi = o.eigenstate(g, n, l)
+            u, _ = o.evolve_nojump(g, phi.astype(np.complex128), 0, l, m, 0, t_steps)
+            A = dr * np.dot(phi, u)
+            E = -np.angle(A) / (t_steps * g.dt)
+            Eex = -M * alpha ** 2 / (4 * n * n)
+            errs[(N, n, l)] = abs(E - Eex) / abs(Eex)
+    assert errs[(2048, 1, 0)] < errs[(512, 1, 0)] / 4
+    assert errs[(2048, 1, 0)] < 1e-4
+    assert errs[(2048, 2, 0)] < 1e-3
+    assert errs[(2048, 2, 1)] < 5e-4
+
+
+def test_nonhermitian_decay_rate(oracle_lib):
+    """With jumps off the norm is p_NoJump(t) and -d|psi|^2/dt = <psi|Gamma|psi> (Eq. wta), with
+    Gamma_s = kappa_hat T^3 r^2 and Gamma_o = (7/16) kappa_hat T^3 r^2 (Sec. 3.4.2, Gamma).  The
+    centred difference of the norm agrees to O(dt^2)."""
+    o = oracle_lib
+    T3 = 0.4 ** 3
+    m = o.medium(T0=0.4, tau0=1e9, Tf=0.39, kappa_hat=5.0, gamma_hat=-1.0)   # T constant over the window
+    for color, frac in ((0, 1.0), (1, 7.0 / 16.0)):
+        errs = []
+        for dt in (0.001, 0.0005):
+            g = o.Grid(N=256, L=10.0, dt=dt)
+            dr = g.L / g.N
+            r = np.arange(g.N) * dr
+            nst = int(round(0.2 / dt))
+            u0 = o.initial_state(g, o.init_spec("gauss", 0.6, 1, 1, color))
+            u, h = o.evolve_nojump(g, u0, color, 1, m, 0, nst)
+            _, h1 = o.evolve_nojump(g, u, color, 1, m, nst, 1)
+            rate = -(h1[0] - h[-2]) / (2 * dt)          # centred at u, the state after step nst-1
+            gam = frac * 5.0 * T3 * dr * np.sum(r * r * np.abs(u) ** 2)
+            errs.append(abs(rate - gam) / gam)
+            assert np.all(np.diff(h) < 0)
+        assert errs[0] < 2e-6
+        assert 3.0 < errs[0] / errs[1] < 5.0            # second order in dt
+
+
+# ------------------------------------------------------------------------------------------------
+# trajectories: waiting-time statistics, shortcut exactness, options
+# ------------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small_batch(oracle_lib):
+    o = oracle_lib
+    g = o.Grid(N=64, L=2.5, dt=0.002)
+    spec = o.init_spec("gauss", 0.3, 1, 0, 0)
+    m = o.medium(T0=0.5, tau0=0.6, Tf=0.42, kappa_hat=4.0, gamma_hat=-1.0)
+    n = 4000
+    obs, nj, _ = o.run_batch(g, [spec], np.zeros(n, int), [m], np.zeros(n, int), np.arange(n, dtype=np.uint64) + 1000)
+    return g, spec, m, obs, nj[0]
+
+
+def test_zero_jump_fraction_is_p_nojump(oracle_lib, small_batch):
+    g, spec, m, obs, nj = small_batch
+    p = nj["norm2"]
+    n = len(obs)
+    frac = np.mean(obs["n_jumps"] == 0)
+    assert 0.05 < p < 0.95
+    assert abs(frac - p) < 3.5 * np.sqrt(p * (1 - p) / n)
+    # zero-jump trajectories are exactly the rMin shortcuts
+    assert np.array_equal(obs["n_jumps"] == 0, (obs["flags"] & oracle_lib.F_NOJUMP_SHORTCUT) != 0)
+
+
+def test_first_jump_time_distribution(oracle_lib, small_batch):
+    """P(first jump after step <= n) = 1 - |psi_nojump(n)|^2 (Eq. wta with a uniform threshold)."""
+    o = oracle_lib
+    g, spec, m, obs, nj = small_batch
+    u0 = o.initial_state(g, spec)
+    _, h = o.evolve_nojump(g, u0, spec.color, spec.l, m, 0, o.n_steps(g, m))
+    fj = obs["first_jump_step"]
+    n = len(fj)
+    steps = np.arange(len(h))
+    emp = np.searchsorted(np.sort(fj[fj >= 0]), steps, side="right") / n
+    D = np.abs(emp - (1 - h)).max()
+    assert D < 1.63 / np.sqrt(n)      # Kolmogorov-Smirnov at the 1% level
+
+
+def test_rmin_shortcut_is_exact(oracle_lib):
+    """A trajectory with r0 < p_NoJump never jumps, so its full evolution equals the zeroth
+    trajectory bit for bit (Sec. 3.5 item 4a)."""
+    o = oracle_lib
+    g = o.Grid(N=64, L=2.5, dt=0.002, use_rmin=0)
+    spec = o.init_spec("gauss", 0.3, 1, 0, 0)
+    m = o.medium(T0=0.5, tau0=0.6, Tf=0.42, kappa_hat=4.0, gamma_hat=-1.0)
+    nj = o.nojump_run(g, spec, m)
+    found = 0
+    for seed in range(200):
+        r0 = o.draws(seed, 0)[0]
+        if r0 < nj["norm2"]:
+            rec = o.trajectory(g, spec, m, seed)
+            assert rec["n_jumps"] == 0
+            for f in ("surv", "ov_re", "ov_im", "norm2"):
+                assert np.array_equal(rec[f], nj[f])
+            found += 1
+            if found == 5:
+                break
+    assert found == 5
+
+
+def test_options_rmax_maxjumps_lcap(oracle_lib):
+    o = oracle_lib
+    spec = o.init_spec("gauss", 0.3, 1, 0, 0)
+    m = o.medium(T0=0.5, tau0=0.6, Tf=0.42, kappa_hat=4.0, gamma_hat=-1.0)
+    seeds = np.arange(300, dtype=np.uint64)
+    base = o.Grid(N=64, L=2.5, dt=0.002)
+    obs, _, _ = o.run_batch(base, [spec], np.zeros(300, int), [m], np.zeros(300, int), seeds)
+    g = o.Grid(N=64, L=2.5, dt=0.002, r_max=0.5)
+    ob2, _, _ = o.run_batch(g, [spec], np.zeros(300, int), [m], np.zeros(300, int), seeds)
+    cut = obs["r0"] > 0.5
+    assert cut.any() and (~cut).any()
+    assert np.all(ob2["surv"][cut] == 0) and np.all(ob2["flags"][cut] & o.F_RMAX)
+    assert np.array_equal(ob2["surv"][~cut], obs["surv"][~cut])
+    g = o.Grid(N=64, L=2.5, dt=0.002, max_jumps=1)
+    ob3, _, _ = o.run_batch(g, [spec], np.zeros(300, int), [m], np.zeros(300, int), seeds)
+    two = obs["n_jumps"] >= 2
+    assert two.any()
+    assert np.all(ob3["flags"][two] & o.F_MAXJUMPS) and np.all(ob3["surv"][two] == 0)
+    assert np.array_equal(ob3["surv"][obs["n_jumps"] <= 1], obs["surv"][obs["n_jumps"] <= 1])
+    g = o.Grid(N=64, L=2.5, dt=0.002, l_cap=1)
+    ob4, _, _ = o.run_batch(g, [spec], np.zeros(300, int), [m], np.zeros(300, int), seeds)
+    assert np.all(ob4["l"][(ob4["flags"] & o.F_LCAP) == 0] <= 1)
+
+
+def test_determinism_and_thread_independence(oracle_lib):
+    from paper_2107_06147_gb300 import inputs
+    o = oracle_lib
+    w = inputs.small_parity(N=32, n_traj=24)
+    g, inits, media = oracle_inputs(w)
+    a, _, ua = o.run_batch(g, inits, w.init_idx, media, w.medium_idx, w.seeds, n_threads=1, want_states=True)
+    b, _, ub = o.run_batch(g, inits, w.init_idx, media, w.medium_idx, w.seeds, n_threads=8, want_states=True)
+    assert a.tobytes() == b.tobytes()
+    assert np.array_equal(ua, ub)
+
+
+# ------------------------------------------------------------------------------------------------
+# the whole unravelling against the density matrix
+# ------------------------------------------------------------------------------------------------
+def test_trajectory_average_matches_lindblad(oracle_lib):
+    """N = 32, l <= 3: the mean survival probabilities and the colour/l populations of 20,000
+    trajectories equal the RK4 solution of the Lindblad equation (Eq. Lindblad with the collapse
+    operators of Eq. collapse) within 3.5 standard errors.  This pins the jump rules, the waiting
+    time, and the normalised read-out of the overlaps."""
+    from oracle import lindblad
+    o = oracle_lib
+    N, L, dt = 32, 8.0, 0.002
+    g = o.Grid(N=N, L=L, dt=dt, l_cap=3)
+    spec = o.init_spec("gauss", 0.5, 1, 0, 0)
+    m = o.medium(T0=0.45, tau0=0.6, Tf=0.35, kappa_hat=3.0, gamma_hat=-1.0)
+    u0 = o.initial_state(g, spec)
+    rho, ns = lindblad.evolve(N, L, dt, g.M, g.alpha_s, g.Nc, u0, 0, 0, 3, m.T0, m.tau0, m.Tf,
+                              m.kappa_hat, m.gamma_hat)
+    assert ns == o.n_steps(g, m)
+    dr = L / N
+    nt = 20000
+    obs, nj, _ = o.run_batch(g, [spec], np.zeros(nt, int), [m], np.zeros(nt, int), np.arange(nt, dtype=np.uint64))
+    basis = [(1, 0), (2, 0), (2, 1), (3, 0), (3, 1), (3, 2)]
+    for s, (n, l) in enumerate(basis):
+        phi = o.eigenstate(g, n, l)
+        expect = lindblad.expectation(rho[0, l], phi, dr)
+        if l == 0:   # survival ratio -> probability
+            o0 = dr * np.dot(phi[1:], u0[1:].real)
+            v = obs["surv"][:, s] * o0 * o0
+        else:
+            v = obs["surv"][:, s]
+        sem = v.std() / np.sqrt(nt)
+        assert abs(v.mean() - expect) < 3.5 * sem + 1e-12, (s, v.mean(), expect, sem)
+    pops = np.real(np.trace(rho, axis1=2, axis2=3))
+    alive = (obs["flags"] & o.F_LCAP) == 0
+    for c in range(2):
+        for l in range(4):
+            f = np.mean((obs["color"] == c) & (obs["l"] == l) & alive)
+            p = pops[c, l]
+            assert abs(f - p) < 3.5 * np.sqrt(max(p * (1 - p), 1e-6) / nt), (c, l, f, p)
