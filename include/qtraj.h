@@ -1,0 +1,170 @@
+/*
+ * qtraj.h -- C ABI of libqtraj, the GB300 (sm_103a) engine for the quantum-trajectory hot path of
+ * QTraj 1.0 (Brambilla et al., arXiv:2107.06147): many independent waiting-time Monte-Carlo
+ * wave-function trajectories of the heavy-quarkonium radial wave function u_l(r) under the
+ * non-Hermitian OQS+pNRQCD Hamiltonian, and their overlaps with the vacuum Coulomb states.
+ *
+ * Conventions shared by every entry point:
+ *   - every call returns a qtraj_status; nothing throws across the ABI; qtraj_last_error() gives
+ *     a message for the last failing call on the calling thread;
+ *   - GPU work is enqueued on the caller's stream (a cudaStream_t passed as void*, NULL = the legacy
+ *     default stream) and is asynchronous unless the call says it synchronises;
+ *   - the caller owns every buffer it passes and the library never frees caller memory; device
+ *     buffers are plain device pointers with byte sizes; the library owns the context and its
+ *     internal read-only tables (twiddles, phase tables, Coulomb basis), which it allocates in
+ *     qtraj_create/qtraj_init and frees in qtraj_destroy;
+ *   - one context is used by one host thread at a time; separate contexts are independent.
+ *
+ * Units: lengths in GeV^-1, energies and temperatures in GeV, proper time tau in fm/c
+ * (hbar c = 0.1973269804 GeV fm converts the step dt to fm/c).
+ */
+#ifndef QTRAJ_H
+#define QTRAJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qtraj_ctx qtraj_ctx;
+
+typedef enum {
+    QTRAJ_OK = 0,
+    QTRAJ_EINVAL = 1,     /* bad argument: sizes, ranges, null pointers, unsupported N */
+    QTRAJ_ENOMEM = 2,     /* workspace too small, or a host/device allocation failed */
+    QTRAJ_ECUDA = 3,      /* a CUDA runtime call failed (message in qtraj_last_error) */
+    QTRAJ_ETIMEOUT = 4,   /* a bounded device wait ran out */
+    QTRAJ_ENONFINITE = 5, /* a trajectory norm became NaN/Inf (flag set in its record) */
+    QTRAJ_EBUSY = 6       /* the context has queued work that this call would overwrite */
+} qtraj_status;
+
+/* arithmetic of the step: the norm, the waiting-time comparison and the overlaps are FP64 in all */
+typedef enum { QTRAJ_FP64 = 0, QTRAJ_FP32 = 1 } qtraj_precision;
+
+/* QTRAJ_FUSED: one persistent kernel; every trajectory stays in shared memory/registers for its
+ *              whole life.  QTRAJ_PLAIN: the plain per-step form, a sequence of separate kernels
+ *              over the whole batch per time step with the state in HBM (FP64 only). */
+typedef enum { QTRAJ_FUSED = 0, QTRAJ_PLAIN = 1 } qtraj_form;
+
+typedef struct {
+    double alpha_s;  /* strong coupling; alpha = C_F alpha_s (Table 1 "alpha"; App. E)            */
+    double Nc;       /* number of colours (App. E: C_F = (Nc^2-1)/(2Nc))                         */
+    int deriv_type;  /* 0: T = p^2/M; 1: T = 2[1-cos(p dr)]/(M dr^2) (Sec. 2.4, Table 1)          */
+    int max_jumps;   /* < 0 unlimited; a jump triggered with n_jumps == max_jumps ends the
+                        trajectory with zero overlaps (Sec. 3.5 item 4b)                         */
+    double r_max;    /* 1.0 = off; r0 > r_max ends the trajectory with zero overlaps (Sec. 3.5)   */
+    int l_cap;       /* < 0 none; a jump to l > l_cap ends the trajectory with zero overlaps
+                        (a truncation used to compare with a density matrix cut at l_cap)        */
+    int use_rmin;    /* 1: rMin shortcut -- r0 < p_NoJump copies the no-jump result (Sec. 3.5)  */
+    int precision;   /* qtraj_precision */
+    int form;        /* qtraj_form */
+    int save_states; /* 1: keep every final u(r) (FP64) in the workspace for qtraj_states()     */
+} qtraj_params;
+
+/* Initial state (Table 1, initType/initWidth/initN/initL/initC): kind 0 is the Gaussian
+ * u = r^{l+1} exp(-r^2/(2 width^2)); kind 1 is the Coulomb eigenstate (n, l).  color 0 = singlet,
+ * 1 = octet.  The state is normalised with the discrete norm (L/N) sum |u_j|^2 = 1 (Eq. normcond). */
+typedef struct {
+    int kind;
+    double width;
+    int n, l, color;
+} qtraj_init_spec;
+
+/* Medium seen by a trajectory.  kind 0 = Bjorken T(tau) = T0 (tau0/tau)^{1/3} from tau0 until
+ * T < Tf (Sec. 3.4, Table 1); kappa_hat >= 0 and gamma_hat <= 0 are the transport coefficients
+ * kappa = kappa_hat T^3, gamma = gamma_hat T^3 of the potential (App. E). */
+typedef struct {
+    int kind;
+    double T0, tau0, Tf;
+    double kappa_hat, gamma_hat;
+} qtraj_medium;
+
+#define QTRAJ_NBASIS 6 /* 1S, 2S, 1P, 3S, 2P, 1D = Coulomb (n,l) (1,0) (2,0) (2,1) (3,0) (3,1) (3,2) */
+
+/* flags of a trajectory record */
+#define QTRAJ_F_NOJUMP_SHORTCUT 1 /* r0 < p_NoJump: the no-jump result was copied              */
+#define QTRAJ_F_BORDERLINE 2      /* |norm^2 - r| < 1e-12 at some waiting-time comparison      */
+#define QTRAJ_F_RMAX 4            /* r0 > r_max                                                */
+#define QTRAJ_F_MAXJUMPS 8        /* ended by max_jumps                                        */
+#define QTRAJ_F_LCAP 16           /* ended by l_cap                                            */
+#define QTRAJ_F_NONFINITE 32      /* norm became NaN/Inf                                       */
+
+/* Result of one trajectory (the ratios.tsv row of App. C plus bookkeeping).  surv[s] is
+ * |<s|psi>|^2 / ||psi||^2 divided by |<s|psi_0>|^2, or undivided when the initial overlap is zero
+ * (App. C footnote), and 0 unless the final state is a singlet of the basis state's l. */
+typedef struct {
+    double surv[QTRAJ_NBASIS];
+    double ov_re[QTRAJ_NBASIS], ov_im[QTRAJ_NBASIS]; /* <s|psi> of the unnormalised final state */
+    double norm2;                                    /* final (L/N) sum |u_j|^2                  */
+    double r0;                                       /* the first waiting-time threshold         */
+    int l, color, n_jumps, n_steps_exec, flags, first_jump_step;
+} qtraj_obs;
+
+/* Create a context for an N-point grid on (0, L] with step dt and heavy-quark mass M (Table 1:
+ * num, L, dt, m).  N must be a power of two in [16, 16384] (FP64 fused: <= 8192).  Builds the
+ * read-only tables on the current CUDA device; synchronous.  EINVAL on N/L/dt/M/params out of
+ * range (alpha_s < 0, Nc < 2, r_max not in (0,1], deriv_type not 0/1, FP32 with the plain form). */
+qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_params *params, qtraj_ctx **out);
+
+/* Frees the context and its tables (synchronises the device first).  NULL is a no-op. */
+void qtraj_destroy(qtraj_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none).  ctx may be NULL. */
+const char *qtraj_last_error(const qtraj_ctx *ctx);
+
+/* Device bytes the caller must provide to qtraj_init for n_traj trajectories (records, per-group
+ * no-jump results, counters, and the state buffers of the plain form / of save_states). */
+size_t qtraj_workspace_bytes(const qtraj_ctx *ctx, int n_traj);
+
+/* Binds the caller's device workspace (>= qtraj_workspace_bytes(ctx, n_traj), 256-byte aligned)
+ * and sets the initial states: trajectory t starts in specs[spec_idx[t]] (spec_idx NULL: all use
+ * specs[0] when n_specs == 1, else spec t when n_specs == n_traj).  Uploads the normalised initial
+ * states and their overlaps with the Coulomb basis (host FP64).  Synchronous. */
+qtraj_status qtraj_init(qtraj_ctx *ctx, void *d_workspace, size_t bytes, int n_traj,
+                        const qtraj_init_spec *specs, int n_specs, const int *spec_idx);
+
+/* Evolves trajectories [0, batch) of the bound workspace through their media: trajectory t sees
+ * media[medium_idx[t]] (same NULL rule as qtraj_init) and draws its waiting-time thresholds and
+ * jump choices from Philox4x32-10 keyed by seeds[t] (host array of batch entries).  With use_rmin,
+ * first evolves one no-jump trajectory per distinct (initial state, medium) pair.  Asynchronous on
+ * `stream`; results are read with qtraj_observables. */
+qtraj_status qtraj_evolve(qtraj_ctx *ctx, int batch, const qtraj_medium *media, int n_media, const int *medium_idx,
+                          const uint64_t *seeds, void *stream);
+
+/* Copies the batch's qtraj_obs records (batch x sizeof(qtraj_obs) bytes) to `out` (host memory if
+ * out_is_device == 0, then the call synchronises `stream`; device memory otherwise).  Returns
+ * QTRAJ_ENONFINITE after a host copy if any trajectory's norm became non-finite. */
+qtraj_status qtraj_observables(qtraj_ctx *ctx, void *out, int out_is_device, void *stream);
+
+/* Copies the final states (batch x N complex128, u_0 = 0) saved with params.save_states = 1. */
+qtraj_status qtraj_states(qtraj_ctx *ctx, void *out, int out_is_device, void *stream);
+
+/* The no-jump results (p_NoJump = norm2) of the last evolve, one per (init spec, medium) pair in
+ * spec-major order (n_specs x n_media records; pairs not used are zero).  Synchronises. */
+qtraj_status qtraj_nojump_results(qtraj_ctx *ctx, qtraj_obs *out_host, int capacity, int *n_written);
+
+/* Counters of the last evolve: steps executed (sum over trajectories, including the no-jump runs),
+ * trajectories run / short-cut, kernel launches, and the device time of the step kernels measured
+ * with events on the caller's stream (valid after a synchronising call). */
+typedef struct {
+    int64_t steps_executed;
+    int64_t nojump_steps;
+    int n_traj, n_shortcut, n_groups;
+    int launches;
+    float ms_nojump, ms_main;
+} qtraj_run_stats;
+qtraj_status qtraj_last_run_stats(qtraj_ctx *ctx, qtraj_run_stats *out);
+
+/* Launch geometry of the fused kernel for this context (threads per trajectory, CTAs per SM,
+ * dynamic shared memory per CTA, registers per thread). */
+typedef struct {
+    int threads_per_traj, ctas_per_sm, smem_bytes, regs_per_thread, radix, sm_count;
+} qtraj_kernel_info;
+qtraj_status qtraj_kernel_info_get(const qtraj_ctx *ctx, qtraj_kernel_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTRAJ_H */

@@ -1,0 +1,647 @@
+// api.cu -- the C ABI of libqtraj (include/qtraj.h): context, read-only tables, workspace layout,
+// and the orchestration of an evolve (no-jump runs of every (initial state, medium) group first,
+// then all trajectories).  All host-side tables are built in FP64.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "fused_launch.cuh"
+#include "plain.cuh"
+#include "qtraj.h"
+
+using namespace qt;
+
+namespace {
+
+constexpr double HBARC = 0.1973269804; // GeV fm
+constexpr double PI = 3.14159265358979323846;
+const int BASIS_N[NBASIS] = {1, 2, 2, 3, 3, 3};
+const int BASIS_L[NBASIS] = {0, 0, 1, 0, 1, 2};
+
+thread_local std::string g_err;
+
+qtraj_status fail(qtraj_status st, const char *fmt, ...)
+{
+    char b[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof b, fmt, ap);
+    va_end(ap);
+    g_err = b;
+    return st;
+}
+
+#define CK(call)                                                                                                   \
+    do {                                                                                                           \
+        cudaError_t e_ = (call);                                                                                   \
+        if (e_ != cudaSuccess) return fail(QTRAJ_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                                           __LINE__);                                                              \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// generalised Laguerre polynomial L_k^{(a)}(x), three-term recurrence
+double laguerre(int k, int a, double x)
+{
+    if (k == 0) return 1.0;
+    double p0 = 1.0, p1 = 1.0 + a - x;
+    for (int i = 1; i < k; ++i) {
+        const double p2 = ((2.0 * i + 1.0 + a - x) * p1 - (i + a) * p0) / (i + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+// discretely normalised Coulomb u_nl = r R_nl on r_j = j dr (j = 0..N-1; u_0 = 0)
+void coulomb_u(int N, double dr, double a0, int n, int l, std::vector<double> &u)
+{
+    u.assign(N, 0.0);
+    double s = 0.0;
+    for (int j = 1; j < N; ++j) {
+        const double r = j * dr;
+        const double v = std::pow(r, l + 1) * std::exp(-r / (n * a0)) * laguerre(n - l - 1, 2 * l + 1, 2.0 * r / (n * a0));
+        u[j] = v;
+        s += v * v;
+    }
+    const double c = 1.0 / std::sqrt(s * dr);
+    for (int j = 1; j < N; ++j) u[j] *= c;
+}
+
+void gauss_u(int N, double dr, double w, int l, std::vector<double> &u)
+{
+    u.assign(N, 0.0);
+    double s = 0.0;
+    for (int j = 1; j < N; ++j) {
+        const double r = j * dr;
+        const double v = std::pow(r, l + 1) * std::exp(-r * r / (2.0 * w * w));
+        u[j] = v;
+        s += v * v;
+    }
+    const double c = 1.0 / std::sqrt(s * dr);
+    for (int j = 1; j < N; ++j) u[j] *= c;
+}
+
+} // namespace
+
+struct qtraj_ctx {
+    int N = 0;
+    double L = 0, dt = 0, M = 0, dr = 0, a0 = 0;
+    qtraj_params p{};
+    int device = 0, sm_count = 0;
+    // read-only tables
+    void *W = nullptr, *KT = nullptr, *sinpre = nullptr, *statV = nullptr;
+    double *eig = nullptr;
+    double *ic = nullptr, *ov0 = nullptr;
+    int *ov0_zero = nullptr, *spec_l = nullptr, *spec_color = nullptr;
+    int n_spec = 0;
+    std::vector<qtraj_init_spec> specs;
+    std::vector<int> spec_idx;
+    MediumDev *media = nullptr;
+    int media_cap = 0;
+    // workspace
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int n_traj = 0;
+    size_t off_trajs = 0, off_obs = 0, off_gtrajs = 0, off_gobs = 0, off_ctr = 0, off_states = 0, off_plain = 0;
+    // host staging and timing
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    cudaEvent_t ev_stage = nullptr, ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    bool evolved = false;
+    int last_batch = 0, last_groups = 0, last_n_media = 0, launches = 0;
+    std::vector<int> group_pair;
+    std::vector<int> host_steps;
+};
+
+namespace {
+
+struct Layout {
+    size_t trajs, obs, gtrajs, gobs, ctr, states, plain, total;
+};
+
+Layout layout(const qtraj_ctx *c, int n)
+{
+    Layout L{};
+    size_t o = 0;
+    L.trajs = o;
+    o = align256(o + sizeof(TrajDev) * (size_t)n);
+    L.obs = o;
+    o = align256(o + sizeof(qtraj_obs) * (size_t)n);
+    L.gtrajs = o;
+    o = align256(o + sizeof(TrajDev) * (size_t)n);
+    L.gobs = o;
+    o = align256(o + sizeof(qtraj_obs) * (size_t)n);
+    L.ctr = o;
+    o = align256(o + 256);
+    L.states = o;
+    if (c->p.save_states) o = align256(o + sizeof(double) * 2 * (size_t)c->N * n);
+    L.plain = o;
+    if (c->p.form == QTRAJ_PLAIN) {
+        o = align256(o + 4 * sizeof(cpx<double>) * (size_t)c->N * n);   // psi, y, z, s
+        o = align256(o + sizeof(double) * (size_t)n);                  // n2
+        o = align256(o + sizeof(PlainState) * (size_t)n);
+    }
+    L.total = o;
+    return L;
+}
+
+template <typename T> qtraj_status build_tables(qtraj_ctx *c)
+{
+    const int N = c->N;
+    std::vector<cpx<T>> W(N), KT(N), stat((size_t)2 * LTAB * N);
+    std::vector<T> sp(N);
+    for (int t = 0; t < N; ++t) {
+        const double a = -2.0 * PI * (double)t / N;
+        W[t] = mk<T>((T)std::cos(a), (T)std::sin(a));
+        sp[t] = (T)std::sin(PI * (double)t / N);
+    }
+    for (int k = 0; k < N; ++k) {
+        const double pk = PI * k / c->L;
+        double Tk = pk * pk / c->M;
+        if (c->p.deriv_type == 1) Tk = 2.0 * (1.0 - std::cos(pk * c->dr)) / (c->M * c->dr * c->dr);
+        const double ph = -Tk * c->dt;
+        KT[k] = mk<T>((T)(std::cos(ph) * 2.0 / N), (T)(std::sin(ph) * 2.0 / N));
+    }
+    const double Nc = c->p.Nc, CF = (Nc * Nc - 1.0) / (2.0 * Nc);
+    const double coul[2] = {-CF * c->p.alpha_s, c->p.alpha_s / (2.0 * Nc)};
+    for (int col = 0; col < 2; ++col)
+        for (int l = 0; l < LTAB; ++l)
+            for (int j = 0; j < N; ++j) {
+                cpx<T> v = mk<T>(0, 0);
+                if (j > 0) {
+                    const double r = j * c->dr;
+                    const double V = coul[col] / r + (double)l * (l + 1) / (c->M * r * r);
+                    const double ph = -V * c->dt * 0.5;
+                    v = mk<T>((T)std::cos(ph), (T)std::sin(ph));
+                }
+                stat[((size_t)col * LTAB + l) * N + j] = v;
+            }
+    CK(cudaMalloc(&c->W, sizeof(cpx<T>) * N));
+    CK(cudaMalloc(&c->KT, sizeof(cpx<T>) * N));
+    CK(cudaMalloc(&c->sinpre, sizeof(T) * N));
+    CK(cudaMalloc(&c->statV, sizeof(cpx<T>) * stat.size()));
+    CK(cudaMemcpy(c->W, W.data(), sizeof(cpx<T>) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->KT, KT.data(), sizeof(cpx<T>) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->sinpre, sp.data(), sizeof(T) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->statV, stat.data(), sizeof(cpx<T>) * stat.size(), cudaMemcpyHostToDevice));
+    return QTRAJ_OK;
+}
+
+template <typename T> Tables<T> tables(const qtraj_ctx *c)
+{
+    Tables<T> t;
+    t.W = (const cpx<T> *)c->W;
+    t.KT = (const cpx<T> *)c->KT;
+    t.sinpre = (const T *)c->sinpre;
+    t.statV = (const cpx<T> *)c->statV;
+    t.eig = c->eig;
+    t.ic = c->ic;
+    t.ov0 = c->ov0;
+    t.ov0_zero = c->ov0_zero;
+    t.spec_l = c->spec_l;
+    t.spec_color = c->spec_color;
+    t.media = c->media;
+    t.dr = c->dr;
+    t.dt = c->dt;
+    t.M = c->M;
+    const double Nc = c->p.Nc;
+    t.p_os = 2.0 / (Nc * Nc - 2.0);
+    t.coul[0] = -(Nc * Nc - 1.0) / (2.0 * Nc) * c->p.alpha_s;
+    t.coul[1] = c->p.alpha_s / (2.0 * Nc);
+    t.max_jumps = c->p.max_jumps;
+    t.l_cap = c->p.l_cap;
+    t.use_rmin = c->p.use_rmin;
+    t.r_max = c->p.r_max;
+    return t;
+}
+
+void free_ptr(void *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+template <typename P> void free_typed(P *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int medium_steps(double dt, const qtraj_medium &m)
+{
+    const double tau_f = m.tau0 * std::pow(m.T0 / m.Tf, 3.0);
+    double s = std::ceil((tau_f - m.tau0) / (HBARC * dt));
+    if (s < 0) s = 0;
+    return (int)s;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *qtraj_last_error(const qtraj_ctx *) { return g_err.c_str(); }
+
+qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_params *params, qtraj_ctx **out)
+{
+    g_err.clear();
+    if (!out || !params) return fail(QTRAJ_EINVAL, "null argument");
+    *out = nullptr;
+    const qtraj_params &p = *params;
+    if (!is_pow2(N) || N < 16 || N > 16384) return fail(QTRAJ_EINVAL, "N=%d must be a power of two in [16, 16384]", N);
+    if (!(L > 0) || !(dt > 0) || !(M > 0)) return fail(QTRAJ_EINVAL, "L, dt and M must be positive");
+    if (!(p.alpha_s >= 0) || !(p.Nc >= 2)) return fail(QTRAJ_EINVAL, "alpha_s >= 0 and Nc >= 2 required");
+    if (p.deriv_type != 0 && p.deriv_type != 1) return fail(QTRAJ_EINVAL, "deriv_type must be 0 or 1");
+    if (!(p.r_max > 0 && p.r_max <= 1)) return fail(QTRAJ_EINVAL, "r_max must be in (0, 1]");
+    if (p.precision != QTRAJ_FP64 && p.precision != QTRAJ_FP32) return fail(QTRAJ_EINVAL, "unknown precision");
+    if (p.form != QTRAJ_FUSED && p.form != QTRAJ_PLAIN) return fail(QTRAJ_EINVAL, "unknown form");
+    if (p.form == QTRAJ_PLAIN && p.precision != QTRAJ_FP64) return fail(QTRAJ_EINVAL, "the plain form is FP64 only");
+    if (p.form == QTRAJ_FUSED && p.precision == QTRAJ_FP64 && N > 8192)
+        return fail(QTRAJ_EINVAL, "the fused FP64 form supports N <= 8192");
+
+    qtraj_ctx *c = new qtraj_ctx();
+    c->N = N;
+    c->L = L;
+    c->dt = dt;
+    c->M = M;
+    c->dr = L / N;
+    c->p = p;
+    c->a0 = 2.0 / (M * (p.Nc * p.Nc - 1.0) / (2.0 * p.Nc) * p.alpha_s);
+    qtraj_status st = QTRAJ_OK;
+    auto bail = [&](qtraj_status s) {
+        qtraj_destroy(c);
+        return s;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(fail(QTRAJ_ECUDA, "no CUDA device"));
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return bail(fail(QTRAJ_ECUDA, "cannot query the SM count"));
+    st = p.precision == QTRAJ_FP32 ? build_tables<float>(c) : build_tables<double>(c);
+    if (st != QTRAJ_OK) return bail(st);
+    std::vector<double> eig((size_t)NBASIS * N), u;
+    for (int s = 0; s < NBASIS; ++s) {
+        coulomb_u(N, c->dr, c->a0, BASIS_N[s], BASIS_L[s], u);
+        std::memcpy(eig.data() + (size_t)s * N, u.data(), sizeof(double) * N);
+    }
+    if (cudaMalloc(&c->eig, sizeof(double) * eig.size()) != cudaSuccess) return bail(fail(QTRAJ_ENOMEM, "cudaMalloc"));
+    if (cudaMemcpy(c->eig, eig.data(), sizeof(double) * eig.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(QTRAJ_ECUDA, "upload of the Coulomb basis failed"));
+    if (cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        cudaEventCreate(&c->ev2) != cudaSuccess)
+        return bail(fail(QTRAJ_ECUDA, "cudaEventCreate failed"));
+    *out = c;
+    return QTRAJ_OK;
+}
+
+void qtraj_destroy(qtraj_ctx *c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_ptr(c->W);
+    free_ptr(c->KT);
+    free_ptr(c->sinpre);
+    free_ptr(c->statV);
+    free_typed(c->eig);
+    free_typed(c->ic);
+    free_typed(c->ov0);
+    free_typed(c->ov0_zero);
+    free_typed(c->spec_l);
+    free_typed(c->spec_color);
+    free_typed(c->media);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->ev_stage) cudaEventDestroy(c->ev_stage);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->ev2) cudaEventDestroy(c->ev2);
+    delete c;
+}
+
+size_t qtraj_workspace_bytes(const qtraj_ctx *c, int n_traj)
+{
+    if (!c || n_traj < 0) return 0;
+    return layout(c, n_traj).total;
+}
+
+qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, const qtraj_init_spec *specs,
+                        int n_specs, const int *spec_idx)
+{
+    g_err.clear();
+    if (!c || !d_ws || !specs) return fail(QTRAJ_EINVAL, "null argument");
+    if (n_traj <= 0 || n_specs <= 0) return fail(QTRAJ_EINVAL, "n_traj and n_specs must be positive");
+    if (((uintptr_t)d_ws & 255) != 0) return fail(QTRAJ_EINVAL, "workspace must be 256-byte aligned");
+    const Layout Lw = layout(c, n_traj);
+    if (bytes < Lw.total) return fail(QTRAJ_ENOMEM, "workspace of %zu bytes < %zu required", bytes, Lw.total);
+    if (!spec_idx && n_specs != 1 && n_specs != n_traj)
+        return fail(QTRAJ_EINVAL, "spec_idx is required unless n_specs is 1 or n_traj");
+    const int N = c->N;
+    for (int s = 0; s < n_specs; ++s) {
+        const qtraj_init_spec &q = specs[s];
+        if (q.kind != 0 && q.kind != 1) return fail(QTRAJ_EINVAL, "spec %d: kind must be 0 or 1", s);
+        if (q.l < 0 || (q.color != 0 && q.color != 1)) return fail(QTRAJ_EINVAL, "spec %d: l >= 0, color 0/1", s);
+        if (q.kind == 0 && !(q.width > 0)) return fail(QTRAJ_EINVAL, "spec %d: width must be positive", s);
+        if (q.kind == 1 && (q.n < 1 || q.l >= q.n)) return fail(QTRAJ_EINVAL, "spec %d: need 0 <= l < n", s);
+    }
+    std::vector<int> idx(n_traj);
+    for (int t = 0; t < n_traj; ++t) {
+        idx[t] = spec_idx ? spec_idx[t] : (n_specs == 1 ? 0 : t);
+        if (idx[t] < 0 || idx[t] >= n_specs) return fail(QTRAJ_EINVAL, "spec_idx[%d] out of range", t);
+    }
+    std::vector<double> ic((size_t)n_specs * N), ov0((size_t)n_specs * NBASIS * 2), u, phi;
+    std::vector<int> zero((size_t)n_specs * NBASIS), sl(n_specs), sc(n_specs);
+    for (int s = 0; s < n_specs; ++s) {
+        const qtraj_init_spec &q = specs[s];
+        if (q.kind == 1) coulomb_u(N, c->dr, c->a0, q.n, q.l, u);
+        else gauss_u(N, c->dr, q.width, q.l, u);
+        std::memcpy(ic.data() + (size_t)s * N, u.data(), sizeof(double) * N);
+        sl[s] = q.l;
+        sc[s] = q.color;
+        for (int b = 0; b < NBASIS; ++b) {
+            const int z = q.color != 0 || q.l != BASIS_L[b] || (q.kind == 1 && q.n != BASIS_N[b]);
+            zero[(size_t)s * NBASIS + b] = z;
+            double o = 0.0;
+            if (!z) {
+                coulomb_u(N, c->dr, c->a0, BASIS_N[b], BASIS_L[b], phi);
+                for (int j = 1; j < N; ++j) o += phi[j] * u[j];
+                o *= c->dr;
+            }
+            ov0[((size_t)s * NBASIS + b) * 2] = o;
+            ov0[((size_t)s * NBASIS + b) * 2 + 1] = 0.0;
+        }
+    }
+    CK(cudaDeviceSynchronize());
+    free_typed(c->ic);
+    free_typed(c->ov0);
+    free_typed(c->ov0_zero);
+    free_typed(c->spec_l);
+    free_typed(c->spec_color);
+    CK(cudaMalloc(&c->ic, sizeof(double) * ic.size()));
+    CK(cudaMalloc(&c->ov0, sizeof(double) * ov0.size()));
+    CK(cudaMalloc(&c->ov0_zero, sizeof(int) * zero.size()));
+    CK(cudaMalloc(&c->spec_l, sizeof(int) * n_specs));
+    CK(cudaMalloc(&c->spec_color, sizeof(int) * n_specs));
+    CK(cudaMemcpy(c->ic, ic.data(), sizeof(double) * ic.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->ov0, ov0.data(), sizeof(double) * ov0.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->ov0_zero, zero.data(), sizeof(int) * zero.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->spec_l, sl.data(), sizeof(int) * n_specs, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->spec_color, sc.data(), sizeof(int) * n_specs, cudaMemcpyHostToDevice));
+    c->specs.assign(specs, specs + n_specs);
+    c->spec_idx = idx;
+    c->n_spec = n_specs;
+    c->ws = (char *)d_ws;
+    c->ws_bytes = bytes;
+    c->n_traj = n_traj;
+    c->off_trajs = Lw.trajs;
+    c->off_obs = Lw.obs;
+    c->off_gtrajs = Lw.gtrajs;
+    c->off_gobs = Lw.gobs;
+    c->off_ctr = Lw.ctr;
+    c->off_states = Lw.states;
+    c->off_plain = Lw.plain;
+    c->evolved = false;
+    return QTRAJ_OK;
+}
+
+qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, int n_media, const int *medium_idx,
+                          const uint64_t *seeds, void *stream)
+{
+    g_err.clear();
+    if (!c || !media || !seeds) return fail(QTRAJ_EINVAL, "null argument");
+    if (!c->ws) return fail(QTRAJ_EINVAL, "qtraj_init has not bound a workspace");
+    if (batch < 0 || batch > c->n_traj) return fail(QTRAJ_EINVAL, "batch %d outside [0, %d]", batch, c->n_traj);
+    if (n_media <= 0) return fail(QTRAJ_EINVAL, "n_media must be positive");
+    if (!medium_idx && n_media != 1 && n_media != batch)
+        return fail(QTRAJ_EINVAL, "medium_idx is required unless n_media is 1 or batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = c->N;
+
+    std::vector<MediumDev> md(n_media);
+    std::vector<int> steps(n_media);
+    const double Nc = c->p.Nc;
+    for (int m = 0; m < n_media; ++m) {
+        const qtraj_medium &q = media[m];
+        if (q.kind != 0) return fail(QTRAJ_EINVAL, "medium %d: only kind 0 (Bjorken) is supported", m);
+        if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return fail(QTRAJ_EINVAL, "medium %d: T0, tau0, Tf > 0", m);
+        if (!(q.kappa_hat >= 0) || !(q.gamma_hat <= 0))
+            return fail(QTRAJ_EINVAL, "medium %d: kappa_hat >= 0 and gamma_hat <= 0 required", m);
+        steps[m] = medium_steps(c->dt, q);
+        md[m].A = q.T0 * q.T0 * q.T0 * q.tau0;
+        md[m].tau0 = q.tau0;
+        md[m].dtau = c->dt * HBARC;
+        for (int col = 0; col < 2; ++col) {
+            const double f = col == 0 ? 0.5 : (Nc * Nc - 2.0) / (4.0 * (Nc * Nc - 1.0));
+            md[m].er[col] = -f * q.kappa_hat * c->dt * 0.5;
+            md[m].ei[col] = -f * q.gamma_hat * c->dt * 0.5;
+        }
+    }
+    std::vector<TrajDev> tr(batch);
+    std::map<std::pair<int, int>, int> gmap;
+    std::vector<TrajDev> gt;
+    std::vector<int> gpair;
+    int max_steps = 0;
+    for (int t = 0; t < batch; ++t) {
+        const int mi = medium_idx ? medium_idx[t] : (n_media == 1 ? 0 : t);
+        if (mi < 0 || mi >= n_media) return fail(QTRAJ_EINVAL, "medium_idx[%d] out of range", t);
+        const int sp = c->spec_idx[t];
+        auto key = std::make_pair(sp, mi);
+        auto it = gmap.find(key);
+        int g;
+        if (it == gmap.end()) {
+            g = (int)gt.size();
+            gmap[key] = g;
+            gt.push_back(TrajDev{0ull, sp, mi, steps[mi], g});
+            gpair.push_back(sp * n_media + mi);
+        } else {
+            g = it->second;
+        }
+        tr[t] = TrajDev{(unsigned long long)seeds[t], sp, mi, steps[mi], g};
+        if (steps[mi] > max_steps) max_steps = steps[mi];
+    }
+    const int n_groups = c->p.use_rmin ? (int)gt.size() : 0;
+
+    // staging: media | trajs | group trajs
+    const size_t b_md = sizeof(MediumDev) * n_media, b_tr = sizeof(TrajDev) * batch, b_gt = sizeof(TrajDev) * gt.size();
+    const size_t need = align256(b_md) + align256(b_tr) + align256(b_gt) + 256;
+    CK(cudaEventSynchronize(c->ev_stage));   // the previous upload has left the staging buffer
+    if (need > c->h_stage_bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        CK(cudaMallocHost(&c->h_stage, need));
+        c->h_stage_bytes = need;
+    }
+    if (n_media > c->media_cap) {
+        CK(cudaStreamSynchronize(s));
+        free_typed(c->media);
+        CK(cudaMalloc(&c->media, sizeof(MediumDev) * n_media));
+        c->media_cap = n_media;
+    }
+    char *h = (char *)c->h_stage;
+    std::memcpy(h, md.data(), b_md);
+    std::memcpy(h + align256(b_md), tr.data(), b_tr);
+    std::memcpy(h + align256(b_md) + align256(b_tr), gt.data(), b_gt);
+    TrajDev *d_tr = (TrajDev *)(c->ws + c->off_trajs);
+    TrajDev *d_gt = (TrajDev *)(c->ws + c->off_gtrajs);
+    qtraj_obs *d_obs = (qtraj_obs *)(c->ws + c->off_obs);
+    qtraj_obs *d_gobs = (qtraj_obs *)(c->ws + c->off_gobs);
+    int *d_ctr = (int *)(c->ws + c->off_ctr);
+    int *d_status = d_ctr + 1;
+    double *d_states = c->p.save_states ? (double *)(c->ws + c->off_states) : nullptr;
+    CK(cudaMemcpyAsync(c->media, h, b_md, cudaMemcpyHostToDevice, s));
+    if (b_tr) CK(cudaMemcpyAsync(d_tr, h + align256(b_md), b_tr, cudaMemcpyHostToDevice, s));
+    if (b_gt) CK(cudaMemcpyAsync(d_gt, h + align256(b_md) + align256(b_tr), b_gt, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->ev_stage, s));
+    CK(cudaMemsetAsync(d_ctr, 0, 256, s));
+
+    c->launches = 0;
+    c->last_batch = batch;
+    c->last_groups = n_groups;
+    c->last_n_media = n_media;
+    c->group_pair = gpair;
+    c->host_steps = steps;
+
+    LaunchArgs ga{d_gt, n_groups, d_gobs, nullptr, d_ctr, d_status, nullptr, 1};
+    LaunchArgs ma{d_tr, batch, d_obs, d_gobs, d_ctr, d_status, d_states, 0};
+    CK(cudaEventRecord(c->ev0, s));
+    if (c->p.form == QTRAJ_PLAIN) {
+        const size_t nN = (size_t)c->n_traj * N;
+        cpx<double> *base = (cpx<double> *)(c->ws + c->off_plain);
+        PlainBuffers pb;
+        pb.psi = base;
+        pb.y = base + nN;
+        pb.z = base + 2 * nN;
+        pb.s = base + 3 * nN;
+        pb.n2 = (double *)(c->ws + align256(c->off_plain + 4 * sizeof(cpx<double>) * nN));
+        pb.st = (PlainState *)((char *)pb.n2 + align256(sizeof(double) * c->n_traj));
+        const Tables<double> tb = tables<double>(c);
+        if (n_groups > 0) {
+            int gmax = 0;
+            for (auto &g : gt) gmax = g.n_steps > gmax ? g.n_steps : gmax;
+            CK(plain_run(tb, ga, N, gmax, pb, s, &c->launches));
+        }
+        CK(cudaEventRecord(c->ev1, s));
+        CK(plain_run(tb, ma, N, max_steps, pb, s, &c->launches));
+    } else {
+        FusedInfo fi;
+        if (c->p.precision == QTRAJ_FP32) {
+            const Tables<float> tb = tables<float>(c);
+            if (n_groups > 0) {
+                CK(fused_launch_f32(N, tb, ga, c->sm_count, 0, s, &fi, false));
+                ++c->launches;
+                CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
+            }
+            CK(cudaEventRecord(c->ev1, s));
+            CK(fused_launch_f32(N, tb, ma, c->sm_count, 0, s, &fi, false));
+        } else {
+            const Tables<double> tb = tables<double>(c);
+            if (n_groups > 0) {
+                CK(fused_launch_f64(N, tb, ga, c->sm_count, 0, s, &fi, false));
+                ++c->launches;
+                CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
+            }
+            CK(cudaEventRecord(c->ev1, s));
+            CK(fused_launch_f64(N, tb, ma, c->sm_count, 0, s, &fi, false));
+        }
+        ++c->launches;
+    }
+    CK(cudaEventRecord(c->ev2, s));
+    c->evolved = true;
+    return QTRAJ_OK;
+}
+
+qtraj_status qtraj_observables(qtraj_ctx *c, void *out, int out_is_device, void *stream)
+{
+    g_err.clear();
+    if (!c || !out) return fail(QTRAJ_EINVAL, "null argument");
+    if (!c->evolved) return fail(QTRAJ_EINVAL, "no evolve has been enqueued");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(qtraj_obs) * c->last_batch;
+    if (bytes) CK(cudaMemcpyAsync(out, c->ws + c->off_obs, bytes, out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!out_is_device) {
+        int status = 0;
+        CK(cudaMemcpyAsync(&status, (int *)(c->ws + c->off_ctr) + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (status & 1) return fail(QTRAJ_ENONFINITE, "a trajectory norm became non-finite");
+    }
+    return QTRAJ_OK;
+}
+
+qtraj_status qtraj_states(qtraj_ctx *c, void *out, int out_is_device, void *stream)
+{
+    g_err.clear();
+    if (!c || !out) return fail(QTRAJ_EINVAL, "null argument");
+    if (!c->p.save_states) return fail(QTRAJ_EINVAL, "the context was created without save_states");
+    if (!c->evolved) return fail(QTRAJ_EINVAL, "no evolve has been enqueued");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * 2 * (size_t)c->N * c->last_batch;
+    if (bytes) CK(cudaMemcpyAsync(out, c->ws + c->off_states, bytes, out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!out_is_device) CK(cudaStreamSynchronize(s));
+    return QTRAJ_OK;
+}
+
+qtraj_status qtraj_nojump_results(qtraj_ctx *c, qtraj_obs *out, int capacity, int *n_written)
+{
+    g_err.clear();
+    if (!c || !out || !n_written) return fail(QTRAJ_EINVAL, "null argument");
+    if (!c->evolved) return fail(QTRAJ_EINVAL, "no evolve has been enqueued");
+    const int n_pairs = c->n_spec * c->last_n_media;
+    if (capacity < n_pairs) return fail(QTRAJ_EINVAL, "capacity %d < %d pairs", capacity, n_pairs);
+    CK(cudaEventSynchronize(c->ev2));
+    std::vector<qtraj_obs> g(c->last_groups);
+    if (c->last_groups) CK(cudaMemcpy(g.data(), c->ws + c->off_gobs, sizeof(qtraj_obs) * c->last_groups, cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(qtraj_obs) * n_pairs);
+    for (int i = 0; i < c->last_groups; ++i) out[c->group_pair[i]] = g[i];
+    *n_written = n_pairs;
+    return QTRAJ_OK;
+}
+
+qtraj_status qtraj_last_run_stats(qtraj_ctx *c, qtraj_run_stats *out)
+{
+    g_err.clear();
+    if (!c || !out) return fail(QTRAJ_EINVAL, "null argument");
+    if (!c->evolved) return fail(QTRAJ_EINVAL, "no evolve has been enqueued");
+    CK(cudaEventSynchronize(c->ev2));
+    std::vector<qtraj_obs> o(c->last_batch);
+    if (c->last_batch) CK(cudaMemcpy(o.data(), c->ws + c->off_obs, sizeof(qtraj_obs) * c->last_batch, cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    for (const qtraj_obs &r : o) {
+        out->steps_executed += r.n_steps_exec;
+        if (r.flags & QTRAJ_F_NOJUMP_SHORTCUT) ++out->n_shortcut;
+    }
+    std::vector<qtraj_obs> g(c->last_groups);
+    if (c->last_groups) CK(cudaMemcpy(g.data(), c->ws + c->off_gobs, sizeof(qtraj_obs) * c->last_groups, cudaMemcpyDeviceToHost));
+    for (const qtraj_obs &r : g) out->nojump_steps += r.n_steps_exec;
+    out->steps_executed += out->nojump_steps;
+    out->n_traj = c->last_batch;
+    out->n_groups = c->last_groups;
+    out->launches = c->launches;
+    CK(cudaEventElapsedTime(&out->ms_nojump, c->ev0, c->ev1));
+    CK(cudaEventElapsedTime(&out->ms_main, c->ev1, c->ev2));
+    return QTRAJ_OK;
+}
+
+qtraj_status qtraj_kernel_info_get(const qtraj_ctx *c, qtraj_kernel_info *out)
+{
+    g_err.clear();
+    if (!c || !out) return fail(QTRAJ_EINVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->sm_count = c->sm_count;
+    if (c->p.form == QTRAJ_PLAIN) return QTRAJ_OK;
+    FusedInfo fi{};
+    LaunchArgs none{};
+    if (c->p.precision == QTRAJ_FP32) CK(fused_launch_f32(c->N, tables<float>(c), none, c->sm_count, 0, nullptr, &fi, true));
+    else CK(fused_launch_f64(c->N, tables<double>(c), none, c->sm_count, 0, nullptr, &fi, true));
+    out->threads_per_traj = fi.G;
+    out->ctas_per_sm = fi.ctas_per_sm;
+    out->smem_bytes = fi.smem;
+    out->regs_per_thread = fi.regs;
+    out->radix = fi.R;
+    return QTRAJ_OK;
+}
+
+} // extern "C"

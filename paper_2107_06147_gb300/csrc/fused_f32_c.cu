@@ -1,0 +1,49 @@
+// fused_f32_c.cu -- float instantiations of the fused trajectory kernel for N in {8192, 16384}.
+#include "fused.cuh"
+#include "fused_launch.cuh"
+
+namespace qt {
+namespace {
+template <int N>
+cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s, FusedInfo *info,
+               bool query_only)
+{
+    auto k = fused_kernel<float, N>;
+    constexpr int G = FusedPlan<N>::G;
+    constexpr int smem = fused_smem_bytes<float, N>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, G, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    if (info) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return e;
+        info->G = G;
+        info->R = FusedPlan<N>::R;
+        info->smem = smem;
+        info->ctas_per_sm = occ;
+        info->regs = fa.numRegs;
+    }
+    if (query_only || a.n_traj <= 0) return cudaSuccess;
+    long grid = (long)sm_count * occ;
+    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+    if (grid > a.n_traj) grid = a.n_traj;
+    k<<<(int)grid, G, smem, s>>>(tb, a);
+    return cudaGetLastError();
+}
+} // namespace
+
+cudaError_t fused_launch_f32_c(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
+                             cudaStream_t s, FusedInfo *info, bool query_only)
+{
+    switch (N) {
+    case 8192: return go<8192>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 16384: return go<16384>(tb, a, sm_count, max_ctas, s, info, query_only);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace qt

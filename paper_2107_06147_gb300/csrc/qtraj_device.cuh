@@ -1,0 +1,261 @@
+// qtraj_device.cuh -- device-side building blocks shared by the fused and the plain forms:
+// complex arithmetic, Philox4x32-10, small in-register DFTs, and the device records.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qtraj.h"
+
+namespace qt {
+
+constexpr int NBASIS = QTRAJ_NBASIS;
+constexpr int LTAB = 64;             // (colour, l) rows of the static space-kernel table
+constexpr double BORDER_EPS = 1e-12; // |norm^2 - r| below this flags a borderline comparison
+
+// ------------------------------------------------------------------------------------------------
+// complex numbers
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct alignas(2 * sizeof(T)) cpx { T x, y; };
+
+template <typename T> __host__ __device__ __forceinline__ cpx<T> mk(T a, T b) { return {a, b}; }
+template <typename T> __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <typename T> __device__ __forceinline__ cpx<T> mul_i(cpx<T> a) { return {-a.y, a.x}; }   // i*a
+template <typename T> __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) { return {a.y, -a.x}; }  // -i*a
+// read-only-cache loads of complex values
+__device__ __forceinline__ cpx<float> ldg(const cpx<float> *p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<double> ldg(const cpx<double> *p)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return {v.x, v.y};
+}
+template <typename T> __device__ __forceinline__ double abs2d(cpx<T> a)
+{
+    return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (k,0,0,0), key = 64-bit seed.
+// Waiting period k of a trajectory uses the four words of counter k: the threshold r from words
+// 0 and 1 (53 bits), the angular-momentum draw u_l from word 2 and the colour draw u_c from word 3.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox10(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        if (i) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+}
+
+struct Draws { double r, ul, uc; };
+
+__device__ __forceinline__ Draws draws(unsigned long long seed, uint32_t k)
+{
+    uint32_t c0 = k, c1 = 0, c2 = 0, c3 = 0;
+    philox10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const unsigned long long w = ((unsigned long long)c1 << 32) | c0;
+    Draws d;
+    d.r = ((double)(w >> 11) + 0.5) * 0x1.0p-53;
+    d.ul = ((double)c2 + 0.5) * 0x1.0p-32;
+    d.uc = ((double)c3 + 0.5) * 0x1.0p-32;
+    return d;
+}
+
+// ------------------------------------------------------------------------------------------------
+// in-register DFTs of size 2, 4, 8, 16: X_k = sum_n x_n exp(-2 pi i n k / R), natural order in/out
+// ------------------------------------------------------------------------------------------------
+// x * exp(-2 pi i j/16) for a compile-time j (after unrolling the switch folds away)
+template <typename T> __device__ __forceinline__ cpx<T> tw16(cpx<T> a, int j)
+{
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, h = (T)0.70710678118654752440;
+    switch (j & 15) {
+    case 0: return a;
+    case 1: return a * mk(c1, -s1);
+    case 2: return scale(mk(a.x + a.y, a.y - a.x), h);
+    case 3: return a * mk(s1, -c1);
+    case 4: return mul_mi(a);
+    case 5: return a * mk(-s1, -c1);
+    case 6: return scale(mk(a.y - a.x, -a.x - a.y), h);
+    case 7: return a * mk(-c1, -s1);
+    case 8: return mk(-a.x, -a.y);
+    case 9: return a * mk(-c1, s1);
+    case 10: return scale(mk(-a.x - a.y, a.x - a.y), h);
+    case 11: return a * mk(-s1, c1);
+    case 12: return mul_i(a);
+    case 13: return a * mk(s1, c1);
+    case 14: return scale(mk(a.x - a.y, a.x + a.y), h);
+    default: return a * mk(c1, s1);
+    }
+}
+
+template <typename T> __device__ __forceinline__ void dft2(cpx<T> &a, cpx<T> &b)
+{
+    const cpx<T> t = a;
+    a = t + b;
+    b = t - b;
+}
+
+template <typename T> __device__ __forceinline__ void dft4(cpx<T> &x0, cpx<T> &x1, cpx<T> &x2, cpx<T> &x3)
+{
+    const cpx<T> a = x0 + x2, b = x0 - x2, c = x1 + x3, d = mul_mi(x1 - x3);
+    x0 = a + c;
+    x2 = a - c;
+    x1 = b + d;
+    x3 = b - d;
+}
+
+// DFT of R = R1*R2 points held at x[base + stride*n]: inner DFTs of size R1 over n1 (n = R2 n1 + n2),
+// twiddles W_R^{n2 k1}, outer DFTs of size R2 over n2; output index k = k1 + R1 k2.
+template <typename T, int R> struct DFT;
+
+template <typename T> struct DFT<T, 1> {
+    template <int S> __device__ __forceinline__ static void run(cpx<T> *) {}
+};
+template <typename T> struct DFT<T, 2> {
+    template <int S> __device__ __forceinline__ static void run(cpx<T> *x) { dft2(x[0], x[S]); }
+};
+template <typename T> struct DFT<T, 4> {
+    template <int S> __device__ __forceinline__ static void run(cpx<T> *x) { dft4(x[0], x[S], x[2 * S], x[3 * S]); }
+};
+template <typename T> struct DFT<T, 8> {
+    template <int S> __device__ __forceinline__ static void run(cpx<T> *x)
+    {
+        // n = 2 n1 + n2: two DFT4 over n1, twiddle W8^{n2 k1}, four DFT2 over n2
+        cpx<T> y[8];
+#pragma unroll
+        for (int n2 = 0; n2 < 2; ++n2) {
+            cpx<T> a = x[(0 + n2) * S], b = x[(2 + n2) * S], c = x[(4 + n2) * S], d = x[(6 + n2) * S];
+            dft4(a, b, c, d);
+            y[n2 * 4 + 0] = a;
+            y[n2 * 4 + 1] = tw16(b, 2 * n2 * 1);
+            y[n2 * 4 + 2] = tw16(c, 2 * n2 * 2);
+            y[n2 * 4 + 3] = tw16(d, 2 * n2 * 3);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            cpx<T> a = y[k1], b = y[4 + k1];
+            dft2(a, b);
+            x[(k1)*S] = a;
+            x[(k1 + 4) * S] = b;
+        }
+    }
+};
+template <typename T> struct DFT<T, 16> {
+    template <int S> __device__ __forceinline__ static void run(cpx<T> *x)
+    {
+        // n = 4 n1 + n2: four DFT4 over n1, twiddle W16^{n2 k1}, four DFT4 over n2
+        cpx<T> y[16];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            cpx<T> a = x[(0 + n2) * S], b = x[(4 + n2) * S], c = x[(8 + n2) * S], d = x[(12 + n2) * S];
+            dft4(a, b, c, d);
+            y[n2 * 4 + 0] = a;
+            y[n2 * 4 + 1] = tw16(b, n2 * 1);
+            y[n2 * 4 + 2] = tw16(c, n2 * 2);
+            y[n2 * 4 + 3] = tw16(d, n2 * 3);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            cpx<T> a = y[k1], b = y[4 + k1], c = y[8 + k1], d = y[12 + k1];
+            dft4(a, b, c, d);
+            x[(k1)*S] = a;
+            x[(k1 + 4) * S] = b;
+            x[(k1 + 8) * S] = c;
+            x[(k1 + 12) * S] = d;
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------------------
+// device records
+// ------------------------------------------------------------------------------------------------
+struct MediumDev {
+    double A;       // T0^3 tau0, so T(tau_n)^3 = A / (tau0 + n dtau)
+    double tau0;    // fm/c
+    double dtau;    // dt * hbar c, fm/c per step
+    double er[2];   // -kappa_c dt/2 per colour: the real exponent of the space kernel is er*T^3*r^2
+    double ei[2];   // -gamma_c dt/2 per colour: the phase of the space kernel is ei*T^3*r^2
+};
+
+struct TrajDev {
+    unsigned long long seed;
+    int spec, medium, n_steps, group;
+};
+
+static_assert(sizeof(qtraj_obs) == 184, "qtraj_obs layout");
+
+// Read-only context tables (device pointers) and scalars.
+template <typename T> struct Tables {
+    const cpx<T> *W;       // N twiddles exp(-2 pi i t / N)
+    const cpx<T> *KT;      // N kinetic factors exp(-i T_kin(p_k) dt) * 2/N, k = 0..N-1
+    const T *sinpre;       // N values sin(pi j / N)
+    const cpx<T> *statV;   // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
+    const double *eig;     // [NBASIS][N] Coulomb basis, discretely normalised
+    const double *ic;      // [n_spec][N] initial states, discretely normalised
+    const double *ov0;     // [n_spec][NBASIS][2] initial overlaps
+    const int *ov0_zero;   // [n_spec][NBASIS] structural zero of the initial overlap
+    const int *spec_l;     // [n_spec]
+    const int *spec_color; // [n_spec]
+    const MediumDev *media;
+    double dr, dt, M, p_os;
+    double coul[2];        // coefficient of 1/r of the colour's Coulomb potential
+    int max_jumps, l_cap, use_rmin;
+    double r_max;
+};
+
+// per-launch arguments of both forms
+struct LaunchArgs {
+    const TrajDev *trajs;
+    int n_traj;
+    qtraj_obs *obs;         // per trajectory (main mode) or per group (no-jump mode)
+    const qtraj_obs *group; // no-jump records read by the shortcut (main mode)
+    int *counter;           // work counter (fused) -- zeroed before the launch
+    int *status;            // bit 0: a non-finite norm was seen
+    double *states;         // optional final states [n_traj][N] complex128
+    int nojump;             // 1: no-jump mode (trajectory t = group t, never jumps)
+};
+
+// static part of the half-step space kernel for (colour, l, j); rows beyond the table are
+// evaluated in FP64 on the fly (rare: l grows by one per jump)
+template <typename T>
+__device__ __forceinline__ cpx<T> static_factor(const Tables<T> &tb, int N, int c, int l, int j)
+{
+    if (l < LTAB) return tb.statV[((size_t)c * LTAB + l) * N + j];
+    if (j == 0) return mk<T>(0, 0);
+    const double r = j * tb.dr;
+    const double V = tb.coul[c] / r + (double)l * (l + 1) / (tb.M * r * r);
+    double s, co;
+    sincos(-V * tb.dt * 0.5, &s, &co);
+    return mk<T>((T)co, (T)s);
+}
+
+// T-dependent part exp((er + i ei) T^3 r^2) of the half-step space kernel
+__device__ __forceinline__ cpx<float> dyn_factor(float er, float ei, float r2)
+{
+    float s, c;
+    sincosf(ei * r2, &s, &c);
+    const float m = expf(er * r2);
+    return mk(m * c, m * s);
+}
+__device__ __forceinline__ cpx<double> dyn_factor(double er, double ei, double r2)
+{
+    double s, c;
+    sincos(ei * r2, &s, &c);
+    const double m = exp(er * r2);
+    return mk(m * c, m * s);
+}
+
+} // namespace qt

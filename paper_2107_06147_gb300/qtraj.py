@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libqtraj (include/qtraj.h).
+
+Argument marshalling only: every step of the trajectory path runs in the library's CUDA kernels.
+PyTorch provides device memory (the workspace) and streams.  Importing this module never falls
+back to anything: if the library is missing or fails to load, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB
+
+NBASIS = 6
+BASIS_NAMES = ("1S", "2S", "1P", "3S", "2P", "1D")
+FP64, FP32 = 0, 1
+FUSED, PLAIN = 0, 1
+F_NOJUMP_SHORTCUT, F_BORDERLINE, F_RMAX, F_MAXJUMPS, F_LCAP, F_NONFINITE = 1, 2, 4, 8, 16, 32
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "EBUSY"}
+
+
+class QtrajError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"qtraj {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int), ("max_jumps", C.c_int),
+                ("r_max", C.c_double), ("l_cap", C.c_int), ("use_rmin", C.c_int), ("precision", C.c_int),
+                ("form", C.c_int), ("save_states", C.c_int)]
+
+
+class InitSpec(C.Structure):
+    _fields_ = [("kind", C.c_int), ("width", C.c_double), ("n", C.c_int), ("l", C.c_int), ("color", C.c_int)]
+
+
+class Medium(C.Structure):
+    _fields_ = [("kind", C.c_int), ("T0", C.c_double), ("tau0", C.c_double), ("Tf", C.c_double),
+                ("kappa_hat", C.c_double), ("gamma_hat", C.c_double)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("steps_executed", C.c_int64), ("nojump_steps", C.c_int64), ("n_traj", C.c_int),
+                ("n_shortcut", C.c_int), ("n_groups", C.c_int), ("launches", C.c_int), ("ms_nojump", C.c_float),
+                ("ms_main", C.c_float)]
+
+
+class KernelInfo(C.Structure):
+    _fields_ = [("threads_per_traj", C.c_int), ("ctas_per_sm", C.c_int), ("smem_bytes", C.c_int),
+                ("regs_per_thread", C.c_int), ("radix", C.c_int), ("sm_count", C.c_int)]
+
+
+OBS_DTYPE = np.dtype([("surv", "<f8", NBASIS), ("ov_re", "<f8", NBASIS), ("ov_im", "<f8", NBASIS),
+                      ("norm2", "<f8"), ("r0", "<f8"), ("l", "<i4"), ("color", "<i4"), ("n_jumps", "<i4"),
+                      ("n_steps_exec", "<i4"), ("flags", "<i4"), ("first_jump_step", "<i4")])
+assert OBS_DTYPE.itemsize == 184
+
+# every entry point of include/qtraj.h with its argument and result types
+_PROTOS = {
+    "qtraj_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(Params), C.POINTER(C.c_void_p)]),
+    "qtraj_destroy": (None, [C.c_void_p]),
+    "qtraj_last_error": (C.c_char_p, [C.c_void_p]),
+    "qtraj_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int]),
+    "qtraj_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.POINTER(InitSpec), C.c_int,
+                             C.POINTER(C.c_int)]),
+    "qtraj_evolve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Medium), C.c_int, C.POINTER(C.c_int),
+                               C.POINTER(C.c_uint64), C.c_void_p]),
+    "qtraj_observables": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "qtraj_states": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "qtraj_nojump_results": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "qtraj_last_run_stats": (C.c_int, [C.c_void_p, C.POINTER(RunStats)]),
+    "qtraj_kernel_info_get": (C.c_int, [C.c_void_p, C.POINTER(KernelInfo)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB):
+    """Loads libqtraj.so (built by build.build()) and declares its prototypes."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"{path} not found: run paper_2107_06147_gb300.build.build() first")
+        L = C.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != 0:
+        raise QtrajError(st, load().qtraj_last_error(ctx).decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+@dataclass
+class Config:
+    N: int = 512
+    L: float = 20.0
+    dt: float = 0.001
+    M: float = 4.65
+    alpha_s: float = 0.3
+    Nc: float = 3.0
+    deriv_type: int = 0
+    max_jumps: int = -1
+    r_max: float = 1.0
+    l_cap: int = -1
+    use_rmin: int = 1
+    precision: int = FP64
+    form: int = FUSED
+    save_states: int = 0
+
+    def params(self) -> Params:
+        return Params(self.alpha_s, self.Nc, self.deriv_type, self.max_jumps, self.r_max, self.l_cap, self.use_rmin,
+                      self.precision, self.form, self.save_states)
+
+
+def init_spec(kind="gauss", width=0.2, n=1, l=0, color=0) -> InitSpec:
+    return InitSpec(0 if kind == "gauss" else 1, width, n, l, color)
+
+
+def medium(T0=0.425, tau0=0.6, Tf=0.25, kappa_hat=5.0, gamma_hat=0.0) -> Medium:
+    return Medium(0, T0, tau0, Tf, kappa_hat, gamma_hat)
+
+
+class Engine:
+    """One libqtraj context plus its workspace (a torch uint8 tensor on the current device)."""
+
+    def __init__(self, cfg: Config):
+        self.cfg = cfg
+        self.lib = load()
+        h = C.c_void_p()
+        p = cfg.params()
+        _check(self.lib.qtraj_create(cfg.N, cfg.L, cfg.dt, cfg.M, C.byref(p), C.byref(h)))
+        self.ctx = h
+        self.ws = None
+        self.n_traj = 0
+        self.batch = 0
+
+    def close(self):
+        if self.ctx:
+            self.lib.qtraj_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, n_traj: int) -> int:
+        return int(self.lib.qtraj_workspace_bytes(self.ctx, n_traj))
+
+    def init(self, specs, n_traj: int, spec_idx=None, workspace=None):
+        """Binds a workspace for n_traj trajectories (allocated with torch unless given) and sets the
+        initial states."""
+        import torch
+        nb = self.workspace_bytes(n_traj)
+        if workspace is None:
+            workspace = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+        self.ws = workspace
+        ptr = workspace.data_ptr()
+        ptr = (ptr + 255) & ~255
+        arr = (InitSpec * len(specs))(*specs)
+        idx = None
+        if spec_idx is not None:
+            self._spec_idx = np.ascontiguousarray(spec_idx, dtype=np.int32)
+            idx = self._spec_idx.ctypes.data_as(C.POINTER(C.c_int))
+        _check(self.lib.qtraj_init(self.ctx, C.c_void_p(ptr), nb, n_traj, arr, len(specs), idx), self.ctx)
+        self.n_traj = n_traj
+
+    def evolve(self, media, seeds, medium_idx=None, batch: int | None = None, stream=None):
+        batch = len(seeds) if batch is None else batch
+        arr = (Medium * len(media))(*media)
+        self._seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        idx = None
+        if medium_idx is not None:
+            self._midx = np.ascontiguousarray(medium_idx, dtype=np.int32)
+            idx = self._midx.ctypes.data_as(C.POINTER(C.c_int))
+        _check(self.lib.qtraj_evolve(self.ctx, batch, arr, len(media), idx,
+                                     self._seeds.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                     C.c_void_p(_stream_ptr(stream))), self.ctx)
+        self.batch = batch
+
+    def observables(self, stream=None, check_finite: bool = True) -> np.ndarray:
+        out = np.zeros(self.batch, dtype=OBS_DTYPE)
+        st = self.lib.qtraj_observables(self.ctx, C.c_void_p(out.ctypes.data), 0, C.c_void_p(_stream_ptr(stream)))
+        if st != 5 or check_finite:
+            _check(st, self.ctx)
+        return out
+
+    def observables_device(self, out_tensor, stream=None):
+        _check(self.lib.qtraj_observables(self.ctx, C.c_void_p(out_tensor.data_ptr()), 1,
+                                          C.c_void_p(_stream_ptr(stream))), self.ctx)
+
+    def states(self, stream=None) -> np.ndarray:
+        out = np.zeros((self.batch, self.cfg.N), dtype=np.complex128)
+        _check(self.lib.qtraj_states(self.ctx, C.c_void_p(out.ctypes.data), 0, C.c_void_p(_stream_ptr(stream))),
+               self.ctx)
+        return out
+
+    def nojump_results(self, n_pairs: int) -> np.ndarray:
+        out = np.zeros(n_pairs, dtype=OBS_DTYPE)
+        nw = C.c_int()
+        _check(self.lib.qtraj_nojump_results(self.ctx, C.c_void_p(out.ctypes.data), n_pairs, C.byref(nw)), self.ctx)
+        return out[: nw.value]
+
+    def stats(self) -> RunStats:
+        s = RunStats()
+        _check(self.lib.qtraj_last_run_stats(self.ctx, C.byref(s)), self.ctx)
+        return s
+
+    def kernel_info(self) -> KernelInfo:
+        k = KernelInfo()
+        _check(self.lib.qtraj_kernel_info_get(self.ctx, C.byref(k)), self.ctx)
+        return k

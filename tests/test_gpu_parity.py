@@ -1,0 +1,217 @@
+"""GPU parity: libqtraj (through its C ABI) against the CPU oracle on the same seeded inputs.
+
+FP64 forms (fused and plain): every trajectory must have the oracle's jump sequence (n_jumps,
+first jump step, final l and colour, flags), final wave functions within 1e-10 relative L2, and
+survival ratios within 1e-10 relative.  Trajectories flagged borderline (|norm^2 - r| < 1e-12 at
+some comparison) on either side are excluded from the sequence identity.
+FP32 fused form: survival ratios within 1e-4 absolute (per trajectory with the same jump sequence),
+final states within 2e-3 relative L2, and at least 90% identical jump sequences.
+"""
+import numpy as np
+import pytest
+
+from conftest import oracle_inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_SURV_TOL = 1e-4
+FP32_STATE_TOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_06147_gb300 import build, qtraj
+    build.build()
+    qtraj.load()
+    return qtraj
+
+
+def run_gpu(q, w, precision, form=0, **cfg):
+    import torch
+    c = q.Config(N=w.grid.N, L=w.grid.L, dt=w.grid.dt, M=w.grid.M, alpha_s=w.grid.alpha_s, Nc=w.grid.Nc,
+                 precision=precision, form=form, save_states=1, **cfg)
+    e = q.Engine(c)
+    e.init([q.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits], w.n_traj, w.init_idx)
+    e.evolve([q.medium(m.T0, m.tau0, m.Tf, m.kappa_hat, m.gamma_hat) for m in w.media], w.seeds, w.medium_idx)
+    obs = e.observables()
+    u = e.states()
+    torch.cuda.synchronize()
+    e.close()
+    return obs, u
+
+
+def run_oracle(w, **cfg):
+    import oracle as o
+    g, inits, media = oracle_inputs(w)
+    for k, v in cfg.items():
+        setattr(g, k, v)
+    ref, nj, u = o.run_batch(g, inits, w.init_idx, media, w.medium_idx, w.seeds, want_states=True)
+    return ref, u
+
+
+def check_fp64(q, obs, ref, u, uref):
+    assert np.array_equal(obs["r0"], ref["r0"])
+    border = ((obs["flags"] | ref["flags"]) & q.F_BORDERLINE) != 0
+    ok = ~border
+    assert ok.mean() > 0.5
+    for f in ("n_jumps", "first_jump_step", "l", "color", "n_steps_exec"):
+        assert np.array_equal(obs[f][ok], ref[f][ok]), (f, obs[f][ok], ref[f][ok])
+    assert np.array_equal(obs["flags"][ok] & ~q.F_BORDERLINE, ref["flags"][ok] & ~q.F_BORDERLINE)
+    ran = ok & (ref["n_steps_exec"] > 0)
+    if ran.any():
+        du = np.linalg.norm(u[ran] - uref[ran], axis=1) / np.linalg.norm(uref[ran], axis=1)
+        assert du.max() < FP64_TOL, du.max()
+    ds = np.abs(obs["surv"][ok] - ref["surv"][ok])
+    assert (ds <= FP64_TOL * np.maximum(1.0, np.abs(ref["surv"][ok]))).all(), ds.max()
+    dn = np.abs(obs["norm2"][ok] - ref["norm2"][ok]) / np.maximum(1e-300, np.abs(ref["norm2"][ok]))
+    assert dn.max() < FP64_TOL
+
+
+def check_fp32(q, obs, ref, u, uref, min_same=0.9):
+    assert np.array_equal(obs["r0"], ref["r0"])
+    same = (obs["n_jumps"] == ref["n_jumps"]) & (obs["first_jump_step"] == ref["first_jump_step"]) & \
+           (obs["l"] == ref["l"]) & (obs["color"] == ref["color"])
+    assert same.mean() >= min_same, same.mean()
+    ds = np.abs(obs["surv"][same] - ref["surv"][same])
+    assert ds.max() <= FP32_SURV_TOL, ds.max()
+    ran = same & (ref["n_steps_exec"] > 0) & ((ref["flags"] & (q.F_LCAP | q.F_MAXJUMPS)) == 0)
+    if ran.any():
+        du = np.linalg.norm(u[ran] - uref[ran], axis=1) / np.linalg.norm(uref[ran], axis=1)
+        assert du.max() < FP32_STATE_TOL, du.max()
+
+
+# ------------------------------------------------------------------------------------------------
+def test_tiny_config_fp64_fused(q):
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.tiny()
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP64)
+    check_fp64(q, obs, ref, u, uref)
+
+
+def test_tiny_config_fp64_plain(q):
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.tiny()
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP64, form=q.PLAIN)
+    check_fp64(q, obs, ref, u, uref)
+
+
+def test_tiny_config_fp32_fused(q):
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.tiny(n_traj=32)
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP32)
+    check_fp32(q, obs, ref, u, uref)
+
+
+@pytest.mark.parametrize("N", [16, 32, 64, 128, 256, 512, 1024, 2048])
+def test_mixed_small_fp64_fused(q, N):
+    """Every FFT plan (radices 4/8/16, one or two middle passes), singlet/octet Gaussian and Coulomb
+    initial states, four media, ragged step counts."""
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=N, n_traj=24, seed=N)
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP64)
+    check_fp64(q, obs, ref, u, uref)
+
+
+@pytest.mark.parametrize("N", [16, 64, 256, 1024])
+def test_mixed_small_fp64_plain(q, N):
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=N, n_traj=24, seed=N + 1)
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP64, form=q.PLAIN)
+    check_fp64(q, obs, ref, u, uref)
+
+
+@pytest.mark.parametrize("N", [16, 64, 512, 4096, 8192, 16384])
+def test_mixed_fp32_fused(q, N):
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=N, n_traj=24 if N <= 4096 else 8, seed=N + 2)
+    if N >= 4096:   # short media keep the oracle fast at large N
+        for m in w.media:
+            m.Tf = m.T0 * 0.97
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP32)
+    check_fp32(q, obs, ref, u, uref, min_same=0.85)
+
+
+def test_large_n_fp64_fused(q):
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=8192, n_traj=6, seed=11)
+    for m in w.media:
+        m.Tf = m.T0 * 0.97
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP64)
+    check_fp64(q, obs, ref, u, uref)
+
+
+@pytest.mark.parametrize("opt", [dict(r_max=0.6), dict(max_jumps=1), dict(l_cap=1), dict(use_rmin=0),
+                                 dict(deriv_type=1)])
+@pytest.mark.parametrize("form", [0, 1])
+def test_options(q, opt, form):
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=64, n_traj=32, seed=5)
+    ref, uref = run_oracle(w, **opt)
+    obs, u = run_gpu(q, w, q.FP64, form=form, **opt)
+    check_fp64(q, obs, ref, u, uref)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_edge_cases(q, form):
+    """A medium that is already below Tf (zero steps), a single trajectory, an octet Coulomb state."""
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=32, n_traj=9, seed=9)
+    w.media[0].Tf = w.media[0].T0 * 1.01          # no step at all
+    w.medium_idx[:3] = 0
+    ref, uref = run_oracle(w)
+    obs, u = run_gpu(q, w, q.FP64, form=form)
+    check_fp64(q, obs, ref, u, uref)
+    assert (ref["n_steps_exec"][:3] == 0).all()
+    one = inputs.small_parity(N=32, n_traj=1, seed=10)
+    ref, uref = run_oracle(one)
+    obs, u = run_gpu(q, one, q.FP64, form=form)
+    check_fp64(q, obs, ref, u, uref)
+
+
+def test_batch_prefix_and_reuse(q):
+    """evolve() on a prefix of the bound trajectories, then again on all of them, on one context."""
+    import torch
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=64, n_traj=16, seed=12)
+    ref, _ = run_oracle(w)
+    e = q.Engine(q.Config(N=64, L=w.grid.L, dt=w.grid.dt))
+    e.init([q.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits], w.n_traj, w.init_idx)
+    media = [q.medium(m.T0, m.tau0, m.Tf, m.kappa_hat, m.gamma_hat) for m in w.media]
+    e.evolve(media, w.seeds[:5], w.medium_idx[:5])
+    a = e.observables()
+    e.evolve(media, w.seeds, w.medium_idx)
+    b = e.observables()
+    torch.cuda.synchronize()
+    e.close()
+    assert len(a) == 5 and len(b) == 16
+    np.testing.assert_allclose(a["surv"], ref["surv"][:5], rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(b["surv"], ref["surv"], rtol=1e-10, atol=1e-14)
+
+
+def test_headline_size_sampled(q):
+    """N = 4096, L = 40, dt = 0.001, 1S/2S/1P thirds, kappa = 5, gamma = 0: a batch of 4096
+    trajectories in the fused FP32 and FP64 forms; 6 sampled trajectories are recomputed by the
+    oracle one by one."""
+    from paper_2107_06147_gb300 import inputs
+    full = inputs.headline(n_traj=4096)
+    sample = np.array([0, 1, 2, 1000, 2047, 4095])
+    sub = inputs.headline(n_traj=4096)
+    sub.init_idx, sub.medium_idx, sub.seeds = full.init_idx[sample], full.medium_idx[sample], full.seeds[sample]
+    ref, uref = run_oracle(sub)
+    obs32, u32 = run_gpu(q, full, q.FP32)
+    check_fp32(q, obs32[sample], ref, u32[sample], uref, min_same=0.8)
+    small = inputs.headline(n_traj=256)
+    obs64, u64 = run_gpu(q, small, q.FP64)
+    s64 = sample[sample < 256]
+    check_fp64(q, obs64[s64], ref[: len(s64)], u64[s64], uref[: len(s64)])
