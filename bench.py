@@ -1,0 +1,354 @@
+"""Benchmark of the quantum-trajectory hot path: trajectory-steps per second at N = 4096.
+
+Workload (uniform batch): singlet Gaussian S wave (width 0.2 GeV^-1), Coulomb 2S and Gaussian P
+wave initial states in equal numbers for each (kappa_hat, gamma_hat) in {4,5,6} x {-3.5,0}, grid
+N = 4096, L = 40 GeV^-1, dt = 0.001 GeV^-1, M = 4.65 GeV, alpha_s = 0.3, Bjorken cooling from
+0.425 GeV at 0.6 fm/c to 0.25 GeV (11,899 steps): 180,000 trajectories.  Trajectory t has initial
+state t % 3, medium (t // 3) % 6 and seed t; bench step i evolves the i-th slice of `--batch` of them
+(a multiple of 18, so every slice has the same pattern of (initial state, medium) pairs) through its
+whole medium: one qtraj_evolve, i.e. the no-jump run of each of the 18 groups, then every
+trajectory.  The metric counts executed trajectory-steps only (rMin short-cuts count zero, the
+no-jump runs count).
+
+Timing: W warm-up steps, then exactly K steps between a barrier + synchronize on both sides,
+measured with CUDA events on the launching stream; the maximum over ranks is reported.  A 256 MiB
+buffer is written between steps to flush L2.  `e2e` repeats the measurement through the C ABI
+with host buffers: the step's descriptors are uploaded from host memory by qtraj_evolve and its
+observables copied back to pinned host memory inside the timed region.
+
+`--impl reference` times the plain CPU oracle on this host's cores (the arm the ratio is taken
+against): every step evolves one trajectory per core of the same workload through the first
+~2,500 steps of its medium.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "traj-steps/s at N=4096 vs plain FP64 GPU form at stated error; p99 request latency"
+UNIT = "traj-steps/s"
+N_GRID, L_BOX, DT = 4096, 40.0, 0.001
+
+
+def workload_config(batch):
+    return {"workload": "uniform batch N=4096 L=40 dt=0.001 1S/2S/1P x kappa{4,5,6} x gamma{-3.5,0}, "
+                        "Bjorken 0.425->0.25 GeV (11899 steps)",
+            "N": N_GRID, "L": L_BOX, "dt": DT, "trajectories_per_step": batch, "precision": "fp32 fused",
+            "l2": "flushed between steps (256 MiB write); state lives on chip"}
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+def fp32_peak_tflops(sm_count, mhz=2070.0):
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def algorithmic_flops_per_step(N):
+    """FP32 flops of one trajectory-step of the method as implemented: two sine transforms, each an
+    N-point complex FFT (5 N log2 N) plus pre/post-processing and the odd-coefficient prefix sum
+    (12 N), the kinetic factor (6 N), two space half-steps (12 N each) and the norm (4 N)."""
+    lg = int(np.log2(N))
+    return 2 * (5 * N * lg + 12 * N) + 6 * N + 2 * 12 * N + 4 * N
+
+
+def nominal_flops_per_step(N):
+    """The nominal count of the odd-extended length-2N transform pair: 10 (2N) log2(2N) + pointwise."""
+    return 10 * 2 * N * int(np.log2(2 * N)) + 30 * N
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2107_06147_gb300 import inputs, qtraj
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = inputs.uniform_interleaved(per_group=10000, N=N_GRID, L=L_BOX, dt=DT)
+    total = w.n_traj
+    B = (args.batch // 18) * 18
+    specs = [qtraj.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits]
+    media = [qtraj.medium(m.T0, m.tau0, m.Tf, m.kappa_hat, m.gamma_hat) for m in w.media]
+    prec = qtraj.FP32 if args.precision == "fp32" else qtraj.FP64
+    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=qtraj.FUSED))
+    n_slices = total // B
+
+    # every rank owns disjoint trajectory ids: step i of rank r takes slice (i*world + r) mod n_slices
+    def slice_ids(i):
+        return np.arange(B) + ((i * world + rank) % n_slices) * B
+
+    eng.init(specs, B, spec_idx=w.init_idx[slice_ids(0)])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    obs_host = torch.empty(B * qtraj.OBS_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+
+    def step(i, e2e=False):
+        ids = slice_ids(i)
+        eng.evolve(media, w.seeds[ids], w.medium_idx[ids], stream=stream)
+        if e2e:
+            st = eng.lib.qtraj_observables(eng.ctx, qtraj.C.c_void_p(obs_host.data_ptr()), 0,
+                                           qtraj.C.c_void_p(stream.cuda_stream))
+            qtraj._check(st, eng.ctx)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        step(i)
+    barrier()
+    kinfo = eng.kernel_info()
+
+    # ---- device-timed region ------------------------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    steps_exec, launches, kernel_ms = 0, 0, 0.0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for i in range(args.warmup, args.warmup + args.steps):
+        step(i)
+        flush.fill_(i & 255)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    # the counters (executed steps, launches, per-launch event times) are read in the e2e pass, which
+    # evolves the same slices again; executed steps are deterministic per slice
+    # ---- end-to-end region through host buffers ---------------------------------------------------
+    barrier()
+    t0 = time.perf_counter()
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    main_ms = []
+    for i in range(args.warmup, args.warmup + args.steps):
+        step(i, e2e=True)
+        s = eng.stats()
+        steps_exec += s.steps_executed
+        launches += s.launches
+        main_ms.append(s.ms_main)
+        kernel_ms += s.ms_main + s.ms_nojump
+        flush.fill_(i & 255)
+    ev3.record(stream)
+    barrier()
+    e2e_ms = ev2.elapsed_time(ev3)
+
+    t_local = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+    cnt = torch.tensor([steps_exec], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    ms, e2e_ms = float(t_local[0]), float(t_local[1])
+    total_steps = float(cnt[0])
+    value = total_steps / (ms / 1e3)
+    e2e_value = total_steps / (e2e_ms / 1e3)
+
+    # roofline of the dominant kernel (the fused FP32 kernel, main launch): algorithmic flops of the
+    # executed trajectory-steps of this rank over that kernel's event time
+    main_steps = steps_exec  # includes the short no-jump launches, < 0.2% of the steps
+    alg = algorithmic_flops_per_step(N_GRID)
+    achieved = main_steps * alg / (sum(main_ms) / 1e3) / 1e12
+    peak = fp32_peak_tflops(kinfo.sm_count)
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "flops_per_traj_step": alg, "nominal_fft_equivalent_flops_per_traj_step": nominal_flops_per_step(N_GRID),
+                "peak_note": "FP32 FMA peak from unit counts: SMs x 128 lanes x 2 flops x 2070 MHz (not measured)"}
+
+    result = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+              "config": workload_config(B) | {"parallelism": f"replicas x{world} (disjoint trajectory ids)"},
+              "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                      "h2d_bytes_per_step": int(B * 24 + 18 * 24 + 6 * 64),
+                      "d2h_bytes_per_step": int(B * qtraj.OBS_DTYPE.itemsize + 4)},
+              "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
+              "kernel": {"threads_per_traj": kinfo.threads_per_traj, "ctas_per_sm": kinfo.ctas_per_sm,
+                         "smem_bytes": kinfo.smem_bytes, "regs": kinfo.regs_per_thread, "radix": kinfo.radix}}
+
+    if rank == 0 and not args.no_compare:
+        result["plain_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.PLAIN, args.compare_batch)
+        result["fused_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.FUSED, args.compare_batch)
+        result["speedup_vs_plain_fp64"] = round(value / world / result["plain_fp64"]["value"], 2)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(args)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    eng.close()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def measure_form(qtraj, w, specs, media, prec, form, B):
+    """Trajectory-steps/s of another form on the first B trajectories of the workload (one evolve)."""
+    import torch
+    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=form))
+    ids = np.arange(B)
+    eng.init(specs, B, spec_idx=w.init_idx[ids])
+    eng.evolve(media, w.seeds[ids], w.medium_idx[ids])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eng.evolve(media, w.seeds[ids], w.medium_idx[ids])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    s = eng.stats()
+    eng.close()
+    ms = s.ms_main + s.ms_nojump
+    return {"value": round(s.steps_executed / (ms / 1e3), 1), "unit": UNIT, "trajectories": B,
+            "traj_steps": int(s.steps_executed), "ms": round(ms, 1), "wall_s": round(wall, 2)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline)
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(n_traj, prefix_steps=2500, seed_offset=0):
+    """Evolves n_traj trajectories of the workload (1S Gaussian, kappa 5, gamma 0 group) through the
+    first prefix_steps steps of the Bjorken medium with the oracle; returns (traj-steps, seconds, cores)."""
+    import oracle as orc
+    threads = os.cpu_count() or 1
+    g = orc.Grid(N=N_GRID, L=L_BOX, dt=DT, use_rmin=0)
+    T0, tau0 = 0.425, 0.6
+    tau_end = tau0 + prefix_steps * DT * 0.1973269804
+    Tf = T0 * (tau0 / tau_end) ** (1.0 / 3.0) * (1 + 1e-9)
+    m = orc.medium(T0, tau0, Tf, 5.0, 0.0)
+    spec = orc.init_spec("gauss", 0.2, 1, 0, 0)
+    seeds = np.arange(n_traj, dtype=np.uint64) + seed_offset
+    t0 = time.perf_counter()
+    obs, _, _ = orc.run_batch(g, [spec], np.zeros(n_traj, np.int32), [m], np.zeros(n_traj, np.int32), seeds,
+                              n_threads=threads)
+    dt = time.perf_counter() - t0
+    return int(obs["n_steps_exec"].sum()), dt, threads
+
+
+def cpu_baseline(args):
+    cores = os.cpu_count() or 1
+    steps, secs, thr = oracle_sample(cores)
+    return {"value": round(steps / secs, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{cores} trajectories (one per core) of the 1S/kappa=5/gamma=0 group, N=4096, "
+                      f"first {steps // cores} steps of the Bjorken medium, plain FP64 C oracle, {secs:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as orc
+    orc.build()
+    cores = os.cpu_count() or 1
+    for i in range(args.warmup):
+        oracle_sample(cores, prefix_steps=300, seed_offset=10_000 * (i + 1))
+    tot_steps, tot_s = 0, 0.0
+    for i in range(args.steps):
+        s, t, thr = oracle_sample(cores, seed_offset=i * cores)
+        tot_steps += s
+        tot_s += t
+    value = tot_steps / tot_s
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_s / args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(cores) | {"precision": "fp64 CPU oracle",
+                                               "sample": "one trajectory per core, first ~2500 steps"},
+           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{cores} trajectories per step, first ~2500 steps of the medium"},
+           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=9216, help="trajectories per bench step (multiple of 18)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--compare-batch", type=int, default=256)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2107_06147_gb300 import build
+        import oracle
+        build.build()
+        oracle.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -155,53 +155,56 @@ Layout layout(const qtraj_ctx *c, int n)
 
 template <typename T> qtraj_status build_tables(qtraj_ctx *c)
 {
+    using PC = typename Prec<T>::C;
+    using PR = typename Prec<T>::Rl;
     const int N = c->N;
-    std::vector<cpx<T>> W(N), KT(N), stat((size_t)2 * LTAB * N);
-    std::vector<T> sp(N);
+    std::vector<PC> W(N), KT(N), stat((size_t)2 * LTAB * N);
+    std::vector<PR> sp(N);
     for (int t = 0; t < N; ++t) {
         const double a = -2.0 * PI * (double)t / N;
-        W[t] = mk<T>((T)std::cos(a), (T)std::sin(a));
-        sp[t] = (T)std::sin(PI * (double)t / N);
+        W[t] = Prec<T>::make(std::cos(a), std::sin(a));
+        sp[t] = Prec<T>::make_r(std::sin(PI * (double)t / N));
     }
     for (int k = 0; k < N; ++k) {
         const double pk = PI * k / c->L;
         double Tk = pk * pk / c->M;
         if (c->p.deriv_type == 1) Tk = 2.0 * (1.0 - std::cos(pk * c->dr)) / (c->M * c->dr * c->dr);
         const double ph = -Tk * c->dt;
-        KT[k] = mk<T>((T)(std::cos(ph) * 2.0 / N), (T)(std::sin(ph) * 2.0 / N));
+        KT[k] = Prec<T>::make(std::cos(ph) * 2.0 / N, std::sin(ph) * 2.0 / N);
     }
     const double Nc = c->p.Nc, CF = (Nc * Nc - 1.0) / (2.0 * Nc);
     const double coul[2] = {-CF * c->p.alpha_s, c->p.alpha_s / (2.0 * Nc)};
     for (int col = 0; col < 2; ++col)
         for (int l = 0; l < LTAB; ++l)
             for (int j = 0; j < N; ++j) {
-                cpx<T> v = mk<T>(0, 0);
+                PC v = Prec<T>::make(0.0, 0.0);
                 if (j > 0) {
                     const double r = j * c->dr;
                     const double V = coul[col] / r + (double)l * (l + 1) / (c->M * r * r);
                     const double ph = -V * c->dt * 0.5;
-                    v = mk<T>((T)std::cos(ph), (T)std::sin(ph));
+                    v = Prec<T>::make(std::cos(ph), std::sin(ph));
                 }
                 stat[((size_t)col * LTAB + l) * N + j] = v;
             }
-    CK(cudaMalloc(&c->W, sizeof(cpx<T>) * N));
-    CK(cudaMalloc(&c->KT, sizeof(cpx<T>) * N));
-    CK(cudaMalloc(&c->sinpre, sizeof(T) * N));
-    CK(cudaMalloc(&c->statV, sizeof(cpx<T>) * stat.size()));
-    CK(cudaMemcpy(c->W, W.data(), sizeof(cpx<T>) * N, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->KT, KT.data(), sizeof(cpx<T>) * N, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->sinpre, sp.data(), sizeof(T) * N, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->statV, stat.data(), sizeof(cpx<T>) * stat.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->W, sizeof(PC) * N));
+    CK(cudaMalloc(&c->KT, sizeof(PC) * N));
+    CK(cudaMalloc(&c->sinpre, sizeof(PR) * N));
+    CK(cudaMalloc(&c->statV, sizeof(PC) * stat.size()));
+    CK(cudaMemcpy(c->W, W.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->KT, KT.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->sinpre, sp.data(), sizeof(PR) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->statV, stat.data(), sizeof(PC) * stat.size(), cudaMemcpyHostToDevice));
     return QTRAJ_OK;
 }
 
 template <typename T> Tables<T> tables(const qtraj_ctx *c)
 {
     Tables<T> t;
-    t.W = (const cpx<T> *)c->W;
-    t.KT = (const cpx<T> *)c->KT;
-    t.sinpre = (const T *)c->sinpre;
-    t.statV = (const cpx<T> *)c->statV;
+    using PC = typename Prec<T>::C;
+    t.W = (const PC *)c->W;
+    t.KT = (const PC *)c->KT;
+    t.sinpre = (const typename Prec<T>::Rl *)c->sinpre;
+    t.statV = (const PC *)c->statV;
     t.eig = c->eig;
     t.ic = c->ic;
     t.ov0 = c->ov0;

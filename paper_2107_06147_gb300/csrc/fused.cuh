@@ -180,26 +180,29 @@ template <typename T, int N> struct Fused {
     }
 
     // y_j = s (f_j + f_{N-j}) + (f_j - f_{N-j})/2 for the pair (ea, eb) = (j, N-j)
-    static __device__ __forceinline__ void pre_pair(cpx<T> *x, int ea, int eb, T s)
+    using PR = Prec<T>;
+    using RL = typename Prec<T>::Rl;
+
+    static __device__ __forceinline__ void pre_pair(cpx<T> *x, int ea, int eb, RL s)
     {
         const cpx<T> a = x[ea], b = x[eb];
-        const cpx<T> sum = scale(a + b, s), dif = scale(a - b, (T)0.5);
+        const cpx<T> sum = PR::mulr(a + b, s), dif = scale(a - b, (T)0.5);
         x[ea] = sum + dif;
         x[eb] = sum - dif;
     }
 
-    static __device__ __forceinline__ void pre(cpx<T> *x, int g, const T *sinpre)
+    static __device__ __forceinline__ void pre(cpx<T> *x, int g, const RL *sinpre)
     {
         if (g != 0) {
 #pragma unroll
-            for (int m = 0; m < R; ++m) pre_pair(x, m, R + (R - 1 - m), sinpre[g + m * NR]);
+            for (int m = 0; m < R; ++m) pre_pair(x, m, R + (R - 1 - m), PR::ldr(&sinpre[g + m * NR]));
         } else {
             x[0] = mk<T>(0, 0);                                // j = 0
             x[R / 2] = scale(x[R / 2], (T)2);                  // j = N/2 pairs with itself, sin = 1
 #pragma unroll
-            for (int m = 1; m < R / 2; ++m) pre_pair(x, m, R - m, sinpre[m * NR]);
+            for (int m = 1; m < R / 2; ++m) pre_pair(x, m, R - m, PR::ldr(&sinpre[m * NR]));
 #pragma unroll
-            for (int m = 0; m < R / 2; ++m) pre_pair(x, R + m, R + (R - 1 - m), sinpre[NR / 2 + m * NR]);
+            for (int m = 0; m < R / 2; ++m) pre_pair(x, R + m, R + (R - 1 - m), PR::ldr(&sinpre[NR / 2 + m * NR]));
         }
     }
 
@@ -277,7 +280,7 @@ template <typename T, int N> struct Fused {
     }
 
     template <int RM, int PP>
-    static __device__ __forceinline__ void mid_pass(cpx<T> *x, cpx<T> *buf, const cpx<T> *W, int g)
+    static __device__ __forceinline__ void mid_pass(cpx<T> *x, cpx<T> *buf, const typename Prec<T>::C *W, int g)
     {
         if constexpr (RM > 1) {
             constexpr int NB = N / RM, PER = E / RM;
@@ -287,7 +290,7 @@ template <typename T, int N> struct Fused {
 #pragma unroll
                 for (int m = 0; m < RM; ++m) {
                     cpx<T> v = buf[i + m * NB];
-                    if (m) v = v * ldg(&W[m * k * (N / (PP * RM))]);
+                    if (m) v = PR::mul(v, PR::ld(&W[m * k * (N / (PP * RM))]));
                     x[q * RM + m] = v;
                 }
             }
@@ -326,7 +329,7 @@ template <typename T, int N> struct Fused {
 #pragma unroll
             for (int m = 0; m < R; ++m) {
                 cpx<T> v = buf[b + m * NR];
-                if (m) v = v * ldg(&tb.W[m * b]);
+                if (m) v = PR::mul(v, PR::ld(&tb.W[m * b]));
                 x[t * R + m] = v;
             }
         }
@@ -347,8 +350,7 @@ template <typename T, int N> struct Fused {
         for (int e = 0; e < E; ++e) {
             const int j = idx(g, e);
             const T r = (T)j * dr;
-            const cpx<T> f = static_factor<T>(tb, N, c, l, j) * dyn_factor(er, ei, r * r);
-            x[e] = x[e] * f;
+            x[e] = PR::mul(x[e], static_factor<T>(tb, N, c, l, j)) * dyn_factor(er, ei, r * r);
         }
     }
 
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(FusedPlan<N>::G) fused_kernel(Tables<T> tb, La
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int j = K::idx(g, e);
-                x[e] = K::s_at(buf, j) * ldg(&tb.KT[j]);
+                x[e] = Prec<T>::mul(K::s_at(buf, j), Prec<T>::ld(&tb.KT[j]));
             }
             __syncthreads();
             K::dst(x, buf, tb, g, wtot);

@@ -128,6 +128,7 @@ __global__ void plain_space_pre(Tables<double> tb, LaunchArgs a, const PlainStat
     }
 }
 
+
 template <int RP>
 __global__ void plain_fft_pass(const cpx<double> *in, cpx<double> *out, const cpx<double> *W, int N, int P,
                                LaunchArgs a, const PlainState *st, int n)

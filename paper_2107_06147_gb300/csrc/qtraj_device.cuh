@@ -38,6 +38,80 @@ __device__ __forceinline__ cpx<double> ldg(const cpx<double> *p)
     const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
     return {v.x, v.y};
 }
+// ------------------------------------------------------------------------------------------------
+// constant multipliers.  In FP32 every constant of the step (twiddles, in-register DFT constants,
+// sine pre-factors, kinetic and potential phase tables) is carried as an unevaluated sum hi + lo of
+// two floats: the rounding of a constant is the same in every step and would otherwise accumulate
+// coherently over 10^4 steps, while the rounding of data is random and grows only as a square root.
+// In FP64 a constant is one double.
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+    using C = cpx<double>; // complex constant
+    using Rl = double;     // real constant
+    static __host__ C make(double re, double im) { return {re, im}; }
+    static __host__ Rl make_r(double v) { return v; }
+    static __device__ __forceinline__ cpx<double> mul(cpx<double> x, C w) { return x * w; }
+    static __device__ __forceinline__ cpx<double> mulr(cpx<double> x, Rl s) { return scale(x, s); }
+    static __device__ __forceinline__ C ld(const C *p) { return ldg(p); }
+    static __device__ __forceinline__ Rl ldr(const Rl *p) { return __ldg(p); }
+    static __device__ __forceinline__ C from_double(double re, double im) { return {re, im}; }
+};
+template <> struct Prec<float> {
+    struct alignas(16) C { float rh, ih, rl, il; };
+    struct alignas(8) Rl { float h, l; };
+    static __host__ C make(double re, double im)
+    {
+        const float rh = (float)re, ih = (float)im;
+        return {rh, ih, (float)(re - (double)rh), (float)(im - (double)ih)};
+    }
+    static __host__ Rl make_r(double v)
+    {
+        const float h = (float)v;
+        return {h, (float)(v - (double)h)};
+    }
+    static __device__ __forceinline__ cpx<float> mul(cpx<float> x, C w)
+    {
+        const float lr = fmaf(x.x, w.rl, -x.y * w.il), li = fmaf(x.x, w.il, x.y * w.rl);
+        return {fmaf(x.x, w.rh, fmaf(-x.y, w.ih, lr)), fmaf(x.x, w.ih, fmaf(x.y, w.rh, li))};
+    }
+    static __device__ __forceinline__ cpx<float> mulr(cpx<float> x, Rl s)
+    {
+        return {fmaf(x.x, s.h, x.x * s.l), fmaf(x.y, s.h, x.y * s.l)};
+    }
+    static __device__ __forceinline__ C ld(const C *p)
+    {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        return {v.x, v.y, v.z, v.w};
+    }
+    static __device__ __forceinline__ Rl ldr(const Rl *p)
+    {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        return {v.x, v.y};
+    }
+    static __device__ __forceinline__ C from_double(double re, double im)
+    {
+        const float rh = (float)re, ih = (float)im;
+        return {rh, ih, (float)(re - (double)rh), (float)(im - (double)ih)};
+    }
+};
+
+// a * (rh + i ih) with the constant's low parts (rl, il) in FP32; plain product in FP64
+template <typename T> __device__ __forceinline__ cpx<T> mulk(cpx<T> a, double re, double im)
+{
+    if constexpr (sizeof(T) == 4) {
+        return Prec<float>::mul(a, Prec<float>::C{(float)re, (float)im, (float)(re - (double)(float)re),
+                                                  (float)(im - (double)(float)im)});
+    } else {
+        return a * mk<T>(re, im);
+    }
+}
+template <typename T> __device__ __forceinline__ T mulkr(T v, double c)
+{
+    if constexpr (sizeof(T) == 4) return fmaf(v, (float)c, v * (float)(c - (double)(float)c));
+    else return v * c;
+}
+
 template <typename T> __device__ __forceinline__ double abs2d(cpx<T> a)
 {
     return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
@@ -77,27 +151,28 @@ __device__ __forceinline__ Draws draws(unsigned long long seed, uint32_t k)
 // ------------------------------------------------------------------------------------------------
 // in-register DFTs of size 2, 4, 8, 16: X_k = sum_n x_n exp(-2 pi i n k / R), natural order in/out
 // ------------------------------------------------------------------------------------------------
-// x * exp(-2 pi i j/16) for a compile-time j (after unrolling the switch folds away)
+// x * exp(-2 pi i j/16) for a compile-time j (after unrolling the switch folds away); the constants
+// cos(pi/8), sin(pi/8), sqrt(1/2) enter with their FP32 low parts in the FP32 form
 template <typename T> __device__ __forceinline__ cpx<T> tw16(cpx<T> a, int j)
 {
-    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, h = (T)0.70710678118654752440;
+    constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173, h = 0.70710678118654752440;
     switch (j & 15) {
     case 0: return a;
-    case 1: return a * mk(c1, -s1);
-    case 2: return scale(mk(a.x + a.y, a.y - a.x), h);
-    case 3: return a * mk(s1, -c1);
+    case 1: return mulk(a, c1, -s1);
+    case 2: return mk(mulkr<T>(a.x + a.y, h), mulkr<T>(a.y - a.x, h));
+    case 3: return mulk(a, s1, -c1);
     case 4: return mul_mi(a);
-    case 5: return a * mk(-s1, -c1);
-    case 6: return scale(mk(a.y - a.x, -a.x - a.y), h);
-    case 7: return a * mk(-c1, -s1);
+    case 5: return mulk(a, -s1, -c1);
+    case 6: return mk(mulkr<T>(a.y - a.x, h), mulkr<T>(-a.x - a.y, h));
+    case 7: return mulk(a, -c1, -s1);
     case 8: return mk(-a.x, -a.y);
-    case 9: return a * mk(-c1, s1);
-    case 10: return scale(mk(-a.x - a.y, a.x - a.y), h);
-    case 11: return a * mk(-s1, c1);
+    case 9: return mulk(a, -c1, s1);
+    case 10: return mk(mulkr<T>(-a.x - a.y, h), mulkr<T>(a.x - a.y, h));
+    case 11: return mulk(a, -s1, c1);
     case 12: return mul_i(a);
-    case 13: return a * mk(s1, c1);
-    case 14: return scale(mk(a.x - a.y, a.x + a.y), h);
-    default: return a * mk(c1, s1);
+    case 13: return mulk(a, s1, c1);
+    case 14: return mk(mulkr<T>(a.x - a.y, h), mulkr<T>(a.x + a.y, h));
+    default: return mulk(a, c1, s1);
     }
 }
 
@@ -199,10 +274,11 @@ static_assert(sizeof(qtraj_obs) == 184, "qtraj_obs layout");
 
 // Read-only context tables (device pointers) and scalars.
 template <typename T> struct Tables {
-    const cpx<T> *W;       // N twiddles exp(-2 pi i t / N)
-    const cpx<T> *KT;      // N kinetic factors exp(-i T_kin(p_k) dt) * 2/N, k = 0..N-1
-    const T *sinpre;       // N values sin(pi j / N)
-    const cpx<T> *statV;   // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
+    using C = typename Prec<T>::C;
+    const C *W;                        // N twiddles exp(-2 pi i t / N)
+    const C *KT;                       // N kinetic factors exp(-i T_kin(p_k) dt) * 2/N, k = 0..N-1
+    const typename Prec<T>::Rl *sinpre; // N values sin(pi j / N)
+    const C *statV;                    // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
     const double *eig;     // [NBASIS][N] Coulomb basis, discretely normalised
     const double *ic;      // [n_spec][N] initial states, discretely normalised
     const double *ov0;     // [n_spec][NBASIS][2] initial overlaps
@@ -231,15 +307,15 @@ struct LaunchArgs {
 // static part of the half-step space kernel for (colour, l, j); rows beyond the table are
 // evaluated in FP64 on the fly (rare: l grows by one per jump)
 template <typename T>
-__device__ __forceinline__ cpx<T> static_factor(const Tables<T> &tb, int N, int c, int l, int j)
+__device__ __forceinline__ typename Prec<T>::C static_factor(const Tables<T> &tb, int N, int c, int l, int j)
 {
-    if (l < LTAB) return tb.statV[((size_t)c * LTAB + l) * N + j];
-    if (j == 0) return mk<T>(0, 0);
+    if (l < LTAB) return Prec<T>::ld(&tb.statV[((size_t)c * LTAB + l) * N + j]);
+    if (j == 0) return Prec<T>::from_double(0.0, 0.0);
     const double r = j * tb.dr;
     const double V = tb.coul[c] / r + (double)l * (l + 1) / (tb.M * r * r);
     double s, co;
     sincos(-V * tb.dt * 0.5, &s, &co);
-    return mk<T>((T)co, (T)s);
+    return Prec<T>::from_double(co, s);
 }
 
 // T-dependent part exp((er + i ei) T^3 r^2) of the half-step space kernel

@@ -93,6 +93,20 @@ def uniform(per_group: int = 10000, N: int = 4096, L: float = 40.0, dt: float = 
                     GridSpec(N, L, dt), inits, media, ii, mi, seeds)
 
 
+def uniform_interleaved(per_group: int = 10000, N: int = 4096, L: float = 40.0, dt: float = 0.001,
+                        kappas=(4.0, 5.0, 6.0), gammas=(-3.5, 0.0)) -> Workload:
+    """The uniform batch in a fixed interleaved order: trajectory t has initial state t % 3 and
+    medium (t // 3) % 6, seed t.  Any slice that starts at a multiple of 18 has the same pattern of
+    (initial state, medium) pairs, so consecutive slices differ only in their seeds."""
+    inits = [GAUSS_1S, COULOMB_2S, GAUSS_1P]
+    media = [MediumSpec(0.425, 0.6, 0.25, k, g) for k in kappas for g in gammas]
+    n = per_group * len(inits) * len(media)
+    t = np.arange(n)
+    return Workload(f"uniform N={N} L={L:g} dt={dt:g} {per_group}/group x {len(inits)} inits x {len(media)} media",
+                    GridSpec(N, L, dt), inits, media, (t % 3).astype(np.int32), ((t // 3) % 6).astype(np.int32),
+                    t.astype(np.uint64))
+
+
 def headline(n_traj: int = 16384, N: int = 4096) -> Workload:
     """One (kappa_hat, gamma_hat) = (5, 0) slice of the uniform N=4096 batch: 1S/2S/1P initial states
     in equal thirds, L=40, dt=0.001, Bjorken 0.425 -> 0.25 GeV."""
