@@ -328,6 +328,30 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_profile_case(args):
+    """One evolve of --batch trajectories of the workload through the first --profile-steps steps of
+    the medium (the fused kernel's steady state at a size a profiler can replay quickly)."""
+    import torch
+
+    from paper_2107_06147_gb300 import inputs, qtraj
+    w = inputs.uniform_interleaved(per_group=10000, N=N_GRID, L=L_BOX, dt=DT)
+    B = max(18, (args.batch // 18) * 18)
+    tau_end = 0.6 + args.profile_steps * DT * 0.1973269804
+    media = [qtraj.medium(m.T0, m.tau0, m.T0 * (m.tau0 / tau_end) ** (1 / 3) * (1 + 1e-9), m.kappa_hat, m.gamma_hat)
+             for m in w.media]
+    prec = qtraj.FP32 if args.precision == "fp32" else qtraj.FP64
+    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=qtraj.FUSED, use_rmin=0))
+    specs = [qtraj.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits]
+    eng.init(specs, B, spec_idx=w.init_idx[:B])
+    for _ in range(2):
+        eng.evolve(media, w.seeds[:B], w.medium_idx[:B])
+    torch.cuda.synchronize()
+    s = eng.stats()
+    print(json.dumps({"profile_case": True, "trajectories": B, "steps_executed": int(s.steps_executed),
+                      "ms": round(s.ms_main, 3), "traj_steps_per_s": round(s.steps_executed / (s.ms_main / 1e3), 1)}))
+    eng.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,7 +363,15 @@ def main():
     ap.add_argument("--compare-batch", type=int, default=256)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
+    ap.add_argument("--profile-steps", type=int, default=200)
     args = ap.parse_args()
+    if args.profile_case:
+        from paper_2107_06147_gb300 import build
+        build.build()
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
