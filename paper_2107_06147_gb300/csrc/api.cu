@@ -97,7 +97,7 @@ struct qtraj_ctx {
     qtraj_params p{};
     int device = 0, sm_count = 0;
     // read-only tables
-    void *W = nullptr, *KT = nullptr, *sinpre = nullptr, *statV = nullptr;
+    void *W = nullptr, *KT = nullptr, *sinpre = nullptr, *statV = nullptr, *statV2 = nullptr;
     double *eig = nullptr;
     double *ic = nullptr, *ov0 = nullptr;
     int *ov0_zero = nullptr, *spec_l = nullptr, *spec_color = nullptr;
@@ -158,7 +158,7 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
     using PC = typename Prec<T>::C;
     using PR = typename Prec<T>::Rl;
     const int N = c->N;
-    std::vector<PC> W(N), KT(N), stat((size_t)2 * LTAB * N);
+    std::vector<PC> W(N), KT(N), stat((size_t)2 * LTAB * N), stat2((size_t)2 * LTAB * N);
     std::vector<PR> sp(N);
     for (int t = 0; t < N; ++t) {
         const double a = -2.0 * PI * (double)t / N;
@@ -177,19 +177,23 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
     for (int col = 0; col < 2; ++col)
         for (int l = 0; l < LTAB; ++l)
             for (int j = 0; j < N; ++j) {
-                PC v = Prec<T>::make(0.0, 0.0);
+                PC v = Prec<T>::make(0.0, 0.0), v2 = v;
                 if (j > 0) {
                     const double r = j * c->dr;
                     const double V = coul[col] / r + (double)l * (l + 1) / (c->M * r * r);
                     const double ph = -V * c->dt * 0.5;
                     v = Prec<T>::make(std::cos(ph), std::sin(ph));
+                    v2 = Prec<T>::make(std::cos(2.0 * ph), std::sin(2.0 * ph));
                 }
                 stat[((size_t)col * LTAB + l) * N + j] = v;
+                stat2[((size_t)col * LTAB + l) * N + j] = v2;
             }
     CK(cudaMalloc(&c->W, sizeof(PC) * N));
     CK(cudaMalloc(&c->KT, sizeof(PC) * N));
     CK(cudaMalloc(&c->sinpre, sizeof(PR) * N));
     CK(cudaMalloc(&c->statV, sizeof(PC) * stat.size()));
+    CK(cudaMalloc(&c->statV2, sizeof(PC) * stat2.size()));
+    CK(cudaMemcpy(c->statV2, stat2.data(), sizeof(PC) * stat2.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->W, W.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->KT, KT.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->sinpre, sp.data(), sizeof(PR) * N, cudaMemcpyHostToDevice));
@@ -205,6 +209,7 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     t.KT = (const PC *)c->KT;
     t.sinpre = (const typename Prec<T>::Rl *)c->sinpre;
     t.statV = (const PC *)c->statV;
+    t.statV2 = (const PC *)c->statV2;
     t.eig = c->eig;
     t.ic = c->ic;
     t.ov0 = c->ov0;
@@ -310,6 +315,7 @@ void qtraj_destroy(qtraj_ctx *c)
     free_ptr(c->KT);
     free_ptr(c->sinpre);
     free_ptr(c->statV);
+    free_ptr(c->statV2);
     free_typed(c->eig);
     free_typed(c->ic);
     free_typed(c->ov0);

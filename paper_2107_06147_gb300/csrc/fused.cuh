@@ -1,28 +1,35 @@
 // fused.cuh -- the fused persistent trajectory kernel.
 //
 // One CTA evolves one trajectory at a time, through every step of its medium, and then fetches the
-// next trajectory from a global work counter.  The wave function never leaves the SM: between steps
-// it lives in registers (2R complex values per thread), and the sine transforms exchange data
-// through one shared-memory buffer of N + N/(2R) complex values.
+// next trajectory from a global work counter.  The wave function never leaves the SM: between the
+// sine transforms it lives in one shared-memory buffer of N + N/R complex values; during a transform
+// each thread holds 2R values in registers.
 //
 // One step (Sec. 3.3, steps 1-5) with T = T(tau_n) (Sec. 3.4, Bjorken):
-//   x <- K_V x                     K_V = exp(-i V_eff dt/2): static table x exp((er + i ei) T^3 r^2)
-//   S = DST(x)                     S_k = sum_j x_j sin(pi j k / N)
-//   S <- K_T S                     K_T = exp(-i T_kin(p_k) dt) * 2/N   (2/N = inverse DST scale)
-//   x = DST(S), x <- K_V x
-//   norm^2 = (L/N) sum |x_j|^2 ; if norm^2 <= r: jump (Sec. 3.2.1, 3.4.3-3.4.4, 3.5)
+//   x <- K_V(n) x        K_V = exp(-i V_eff dt/2) = static(c, l, r) * exp((er + i ei) T^3 r^2)
+//   S = DST(x)           S_k = sum_j x_j sin(pi j k / N)
+//   S <- K_T S           K_T = exp(-i T_kin(p_k) dt) * 2/N   (2/N = inverse DST scale)
+//   x = DST(S)
+//   x <- K_V(n) x, norm^2 = (L/N) sum |x_j|^2, jump if norm^2 <= r (Sec. 3.2.1, 3.4.3-3.4.4, 3.5)
+// The end half-step of step n and the start half-step of step n+1 are applied as one factor
+// static^2 * exp((er_n + er_{n+1}) r^2 + i (ei_n + ei_{n+1}) r^2); the norm after the end half-step is
+// accumulated with the weights |K_V(n)|^2 = exp(2 er_n r^2) on the way.  On the rare steps that
+// jump, the start half-step is turned into the new colour's and l's afterwards (all these factors are
+// diagonal in r and commute with the jump's multiplication by r).
 //
 // The DST-I of the N-point complex vector f (f_0 = f_N = 0) is computed with one N-point complex FFT:
 //   y_j = sin(pi j/N)(f_j + f_{N-j}) + (f_j - f_{N-j})/2,   Y = FFT_N(y),
 //   S_{2k}   = (i/2)(Y_k - Y_{N-k}),
 //   S_{2k+1} = S_{2k-1} + (Y_k + Y_{N-k})/2,  S_{-1} = -S_1    (a prefix sum over k < N/2).
-// This equals the length-2N FFT of the odd extension (the paper's "Fourier sine series" with the
-// wall at r = L) at half its arithmetic and memory.
+// This equals the length-2N FFT of the odd extension (the paper's sine series with the wall at
+// r = L) at half its arithmetic and memory.  In shared memory S is kept as S_{2k} at [k] and S_{2k+1}
+// at [N/2 + k + k/R] (the padded "odd area").
 //
-// FFT: Stockham autosort with radices R (first pass), MID = N/R^2 split in passes of <= 16, R (last).
+// FFT: Stockham autosort with radices R (first pass), MID = N/R^2 in passes of <= 16, R (last).
 // Thread g of G = N/(2R) owns butterflies b1 = g, b2 = N/R - g (g = 0: 0 and N/(2R)) of the first
 // and last passes, i.e. the indices b + m N/R, m < R.  Those index sets are closed under j -> N - j,
-// so the DST pre- and post-processing, which pair j with N - j, stay inside a thread's registers.
+// so the pre- and post-processing, which pair j with N - j, stay inside a thread's registers.
+// Shared-memory addresses of the FFT passes are padded by one element every R.
 #pragma once
 #include "qtraj_device.cuh"
 
@@ -35,15 +42,14 @@ template <int N> struct FusedPlan {
     static constexpr int MID = N / (R * R);      // product of the middle radices
     static constexpr int M1 = MID >= 16 ? 16 : MID;
     static constexpr int M2 = MID / M1;          // 1, 2 or 4
-    static constexpr int SCAN_PAD = R + 1;       // padded chunk of the odd-coefficient scan
-    static constexpr int BUF = N + N / (2 * R) + 8;
+    static constexpr int BUF = N + N / R + 8;    // padded FFT extent; also holds the E/odd layout
     static_assert(N == R * M1 * M2 * R, "plan");
 };
 
 // ------------------------------------------------------------------------------------------------
 // accumulators: FP32 forms accumulate sums of squares in double-float (error-free transformations
-// in FP32), so that norms carry FP64-level accuracy without using GB300's narrow FP64 pipe in the
-// step loop; FP64 forms accumulate in double.
+// in FP32), so norms carry FP64-level accuracy without GB300's narrow FP64 pipe in the step loop;
+// FP64 forms accumulate in double.
 // ------------------------------------------------------------------------------------------------
 struct DF { float hi, lo; };
 
@@ -61,11 +67,10 @@ __device__ __forceinline__ DF df_add(DF a, DF b)
     const float hi = s.hi + t;
     return {hi, t - (hi - s.hi)};
 }
-__device__ __forceinline__ DF df_add_sq(DF a, float v)   // a + v*v, the square split exactly
+__device__ __forceinline__ DF df_add_f(DF a, float p, float e)   // a + (p + e)
 {
-    const float p = v * v, e = fmaf(v, v, -p);
     DF s = two_sum(a.hi, p);
-    const float t = s.lo + a.lo + e;
+    const float t = s.lo + (a.lo + e);
     const float hi = s.hi + t;
     return {hi, t - (hi - s.hi)};
 }
@@ -73,7 +78,16 @@ __device__ __forceinline__ DF df_add_sq(DF a, float v)   // a + v*v, the square 
 template <typename T> struct SqAcc;
 template <> struct SqAcc<float> {
     DF v{0.f, 0.f};
-    __device__ __forceinline__ void add(cpx<float> a) { v = df_add_sq(df_add_sq(v, a.x), a.y); }
+    // v += w |a|^2, the squares and the product with w split exactly
+    __device__ __forceinline__ void add_w(cpx<float> a, float w)
+    {
+        const float px = a.x * a.x, ex = fmaf(a.x, a.x, -px);
+        const float py = a.y * a.y, ey = fmaf(a.y, a.y, -py);
+        const DF s = two_sum(px, py);
+        const float sl = s.lo + ex + ey;
+        const float p = s.hi * w, ep = fmaf(s.hi, w, -p) + sl * w;
+        v = df_add_f(v, p, ep);
+    }
     __device__ __forceinline__ void shfl_add(unsigned mask, int off, int w)
     {
         DF o{__shfl_xor_sync(mask, v.hi, off, w), __shfl_xor_sync(mask, v.lo, off, w)};
@@ -83,38 +97,38 @@ template <> struct SqAcc<float> {
 };
 template <> struct SqAcc<double> {
     double v = 0.0;
-    __device__ __forceinline__ void add(cpx<double> a) { v = fma(a.x, a.x, fma(a.y, a.y, v)); }
+    __device__ __forceinline__ void add_w(cpx<double> a, double w) { v = fma(w, fma(a.x, a.x, a.y * a.y), v); }
     __device__ __forceinline__ void shfl_add(unsigned mask, int off, int w) { v += __shfl_xor_sync(mask, v, off, w); }
     __device__ __forceinline__ double value() const { return v; }
 };
 
-// compensated complex prefix element for the odd-coefficient scan
-template <typename T> struct ScanVal;
-template <> struct ScanVal<float> {
+// compensated complex value for the scan's carries between threads
+template <typename T> struct Carry;
+template <> struct Carry<float> {
     DF re{0.f, 0.f}, im{0.f, 0.f};
-    __device__ __forceinline__ void add(cpx<float> a) { re = df_add(re, DF{a.x, 0.f}); im = df_add(im, DF{a.y, 0.f}); }
-    __device__ __forceinline__ void add(const ScanVal &o) { re = df_add(re, o.re); im = df_add(im, o.im); }
-    __device__ __forceinline__ cpx<float> plus(cpx<float> a) const   // (a + this) rounded once
+    __device__ __forceinline__ void add(cpx<float> a) { re = df_add_f(re, a.x, 0.f); im = df_add_f(im, a.y, 0.f); }
+    __device__ __forceinline__ void add(const Carry &o) { re = df_add(re, o.re); im = df_add(im, o.im); }
+    __device__ __forceinline__ cpx<float> plus(cpx<float> a) const   // (this + a) rounded once
     {
-        const DF r = df_add(re, DF{a.x, 0.f}), i = df_add(im, DF{a.y, 0.f});
+        const DF r = df_add_f(re, a.x, 0.f), i = df_add_f(im, a.y, 0.f);
         return mk(r.hi + r.lo, i.hi + i.lo);
     }
-    __device__ __forceinline__ ScanVal shfl_up(unsigned mask, int off, int w) const
+    __device__ __forceinline__ Carry shfl_up(unsigned mask, int off, int w) const
     {
-        ScanVal o;
+        Carry o;
         o.re = DF{__shfl_up_sync(mask, re.hi, off, w), __shfl_up_sync(mask, re.lo, off, w)};
         o.im = DF{__shfl_up_sync(mask, im.hi, off, w), __shfl_up_sync(mask, im.lo, off, w)};
         return o;
     }
 };
-template <> struct ScanVal<double> {
+template <> struct Carry<double> {
     double re = 0.0, im = 0.0;
     __device__ __forceinline__ void add(cpx<double> a) { re += a.x; im += a.y; }
-    __device__ __forceinline__ void add(const ScanVal &o) { re += o.re; im += o.im; }
-    __device__ __forceinline__ cpx<double> plus(cpx<double> a) const { return mk(a.x + re, a.y + im); }
-    __device__ __forceinline__ ScanVal shfl_up(unsigned mask, int off, int w) const
+    __device__ __forceinline__ void add(const Carry &o) { re += o.re; im += o.im; }
+    __device__ __forceinline__ cpx<double> plus(cpx<double> a) const { return mk(re + a.x, im + a.y); }
+    __device__ __forceinline__ Carry shfl_up(unsigned mask, int off, int w) const
     {
-        ScanVal o;
+        Carry o;
         o.re = __shfl_up_sync(mask, re, off, w);
         o.im = __shfl_up_sync(mask, im, off, w);
         return o;
@@ -143,14 +157,14 @@ template <int G> __device__ __forceinline__ double cross_warp(double v, double *
     }
 }
 
-// sum over the G threads of a trajectory (deterministic order)
+// sum over the G threads of a trajectory (deterministic order, one value in every thread)
 template <int G> __device__ __forceinline__ double slot_sum(double v, double *red)
 {
     constexpr int W = G < 32 ? G : 32;
     const unsigned mask = lane_mask<G>();
 #pragma unroll
     for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, W);
-    if constexpr (G <= 32) v = __shfl_sync(mask, v, 0, W);   // one value for every lane
+    if constexpr (G <= 32) v = __shfl_sync(mask, v, 0, W);
     return cross_warp<G>(v, red);
 }
 
@@ -165,24 +179,81 @@ template <typename T, int G> __device__ __forceinline__ double slot_norm(SqAcc<T
     return cross_warp<G>(v, red);
 }
 
+// exp(x) and (cos, sin)(pi y): the pi-scaled form has no large-argument reduction path
+__device__ __forceinline__ float k_exp(float x) { return expf(x); }
+__device__ __forceinline__ double k_exp(double x) { return exp(x); }
+__device__ __forceinline__ void k_sincospi(float y, float *s, float *c) { sincospif(y, s, c); }
+__device__ __forceinline__ void k_sincospi(double y, double *s, double *c) { sincospi(y, s, c); }
+
+// static factor of a (colour, l) row beyond the table, evaluated in FP64 (rare: l grows by one per
+// jump); span 1 = half step, 2 = full step
+template <typename T>
+__device__ __noinline__ typename Prec<T>::C static_far(double coul, double M, double dt, int l, double r, double span)
+{
+    const double V = coul / r + (double)l * (l + 1) / (M * r * r);
+    double s, c;
+    sincos(-V * dt * 0.5 * span, &s, &c);
+    return Prec<T>::from_double(c, s);
+}
+
+// in-place DFT of RR values (natural order in); output k lands in slot operm(k)
+template <typename T, int RR> struct DFTI {
+    static __device__ __forceinline__ constexpr int operm(int k)
+    {
+        if constexpr (RR == 16) return (k % 4) * 4 + k / 4;
+        else if constexpr (RR == 8) return (k % 4) * 2 + k / 4;
+        else return k;
+    }
+    static __device__ __forceinline__ void run(cpx<T> *x)
+    {
+        if constexpr (RR == 16) {
+#pragma unroll
+            for (int n2 = 0; n2 < 4; ++n2) {
+                dft4(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);       // k1 of column n2 at slot n2 + 4 k1
+                x[4 + n2] = tw16(x[4 + n2], n2 * 1);
+                x[8 + n2] = tw16(x[8 + n2], n2 * 2);
+                x[12 + n2] = tw16(x[12 + n2], n2 * 3);
+            }
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) dft4(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+        } else if constexpr (RR == 8) {
+#pragma unroll
+            for (int n2 = 0; n2 < 2; ++n2) {
+                dft4(x[n2], x[2 + n2], x[4 + n2], x[6 + n2]);        // k1 of column n2 at slot n2 + 2 k1
+                x[2 + n2] = tw16(x[2 + n2], 2 * n2 * 1);
+                x[4 + n2] = tw16(x[4 + n2], 2 * n2 * 2);
+                x[6 + n2] = tw16(x[6 + n2], 2 * n2 * 3);
+            }
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) dft2(x[2 * k1], x[2 * k1 + 1]);
+        } else if constexpr (RR == 4) {
+            dft4(x[0], x[1], x[2], x[3]);
+        } else if constexpr (RR == 2) {
+            dft2(x[0], x[1]);
+        }
+    }
+};
+
 // ------------------------------------------------------------------------------------------------
-// the kernel
+// the sine transform
 // ------------------------------------------------------------------------------------------------
 template <typename T, int N> struct Fused {
     using P = FusedPlan<N>;
+    using PR = Prec<T>;
+    using C = typename Prec<T>::C;
+    using RL = typename Prec<T>::Rl;
     static constexpr int R = P::R, G = P::G, NR = P::NR, E = 2 * R;
+    using DR = DFTI<T, R>;
 
+    static __device__ __forceinline__ int pad(int j) { return j + j / R; }
+    static __device__ __forceinline__ int odd_pos(int k) { return N / 2 + k + k / R; }
+    static __device__ __forceinline__ int b_of(int g, int t) { return t == 0 ? (g == 0 ? 0 : g) : (g == 0 ? NR / 2 : NR - g); }
     // global index of register element e (first/last-pass layout)
-    static __device__ __forceinline__ int idx(int g, int e)
-    {
-        const int b = (e < R) ? (g == 0 ? 0 : g) : (g == 0 ? NR / 2 : NR - g);
-        return b + (e % R) * NR;
-    }
+    static __device__ __forceinline__ int idx(int g, int e) { return b_of(g, e / R) + (e % R) * NR; }
+    // shared-memory position of S_j in the E/odd layout
+    static __device__ __forceinline__ int s_pos(int j) { return (j & 1) ? odd_pos(j >> 1) : (j >> 1); }
 
     // y_j = s (f_j + f_{N-j}) + (f_j - f_{N-j})/2 for the pair (ea, eb) = (j, N-j)
-    using PR = Prec<T>;
-    using RL = typename Prec<T>::Rl;
-
     static __device__ __forceinline__ void pre_pair(cpx<T> *x, int ea, int eb, RL s)
     {
         const cpx<T> a = x[ea], b = x[eb];
@@ -206,56 +277,57 @@ template <typename T, int N> struct Fused {
         }
     }
 
-    // E_k = (i/2)(Y_k - Y_{N-k}) -> buf[k];  C_k = (Y_k + Y_{N-k})/2 (C_0 halved) -> odd area
-    static __device__ __forceinline__ int odd_pos(int k) { return N / 2 + k + k / R; }
-
+    // E_k = (i/2)(Y_k - Y_{N-k}) -> [k];  C_k = (Y_k + Y_{N-k})/2 (C_0 halved) -> odd area
     static __device__ __forceinline__ void post_pair(cpx<T> *buf, int k, cpx<T> A, cpx<T> B)
     {
         buf[k] = mul_i(scale(A - B, (T)0.5));
         buf[odd_pos(k)] = scale(A + B, (T)0.5);
     }
 
+    // Y at index b_t + m NR is in register slot t R + operm(m) after the last pass
+    static __device__ __forceinline__ cpx<T> Y(const cpx<T> *x, int t, int m) { return x[t * R + DR::operm(m)]; }
+
     static __device__ __forceinline__ void post(const cpx<T> *x, int g, cpx<T> *buf)
     {
         if (g != 0) {
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                const int eb = R + (R - 1 - m);
-                if (m < R / 2) post_pair(buf, g + m * NR, x[m], x[eb]);
-                else post_pair(buf, (NR - g) + (R - 1 - m) * NR, x[eb], x[m]);
+                if (m < R / 2) post_pair(buf, g + m * NR, Y(x, 0, m), Y(x, 1, R - 1 - m));
+                else post_pair(buf, (NR - g) + (R - 1 - m) * NR, Y(x, 1, R - 1 - m), Y(x, 0, m));
             }
         } else {
             buf[0] = mk<T>(0, 0);
-            buf[odd_pos(0)] = scale(x[0], (T)0.5);             // S_1 = C_0 / 2 = Y_0 / 2
+            buf[odd_pos(0)] = scale(Y(x, 0, 0), (T)0.5);      // S_1 = C_0 / 2 = Y_0 / 2
 #pragma unroll
-            for (int m = 1; m < R / 2; ++m) post_pair(buf, m * NR, x[m], x[R - m]);
+            for (int m = 1; m < R / 2; ++m) post_pair(buf, m * NR, Y(x, 0, m), Y(x, 0, R - m));
 #pragma unroll
-            for (int m = 0; m < R / 2; ++m) post_pair(buf, NR / 2 + m * NR, x[R + m], x[R + (R - 1 - m)]);
+            for (int m = 0; m < R / 2; ++m) post_pair(buf, NR / 2 + m * NR, Y(x, 1, m), Y(x, 1, R - 1 - m));
         }
     }
 
-    // inclusive prefix sum of the N/2 odd-area values: thread g owns k in [gR, gR + R)
-    static __device__ __forceinline__ void scan(cpx<T> *buf, int g, ScanVal<T> *wtot)
+    // inclusive prefix sum of the N/2 odd-area values: thread g owns the chunk k in [gR, gR + R).
+    // Chunk totals and the carries between chunks are compensated (a rounding error there would reach
+    // every later coefficient); the running sum inside a chunk is plain and only reaches its chunk.
+    static __device__ __forceinline__ void scan(cpx<T> *buf, int g, Carry<T> *wtot)
     {
         constexpr int W = G < 32 ? G : 32;
         const unsigned mask = lane_mask<G>();
-        cpx<T> *p = buf + N / 2 + g * P::SCAN_PAD;
+        cpx<T> *p = buf + odd_pos(g * R);
         cpx<T> v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) v[q] = p[q];
-        ScanVal<T> run;                 // compensated chunk total
+        Carry<T> tot;
 #pragma unroll
-        for (int q = 0; q < R; ++q) run.add(v[q]);
-        // exclusive scan of chunk totals across the trajectory's threads
+        for (int q = 0; q < R; ++q) tot.add(v[q]);
         const int lane = threadIdx.x & (W - 1);
-        ScanVal<T> inc = run;
+        Carry<T> inc = tot;
 #pragma unroll
         for (int off = 1; off < W; off <<= 1) {
-            ScanVal<T> y = inc.shfl_up(mask, off, W);
+            Carry<T> y = inc.shfl_up(mask, off, W);
             if (lane >= off) inc.add(y);
         }
-        ScanVal<T> excl = inc.shfl_up(mask, 1, W);
-        if (lane == 0) excl = ScanVal<T>();
+        Carry<T> excl = inc.shfl_up(mask, 1, W);
+        if (lane == 0) excl = Carry<T>();
         if constexpr (G > 32) {
             const int warp = threadIdx.x >> 5;
             if (lane == 31) wtot[warp] = inc;
@@ -263,24 +335,16 @@ template <typename T, int N> struct Fused {
 #pragma unroll 1
             for (int w = 0; w < warp; ++w) excl.add(wtot[w]);
         }
-        // the chunk's running sum continues from the carried offset in compensated arithmetic, so
-        // every output is rounded once
-        ScanVal<T> acc = excl;
+        cpx<T> run = mk<T>(0, 0);
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            acc.add(v[q]);
-            p[q] = acc.plus(mk<T>(0, 0));
+            run = run + v[q];
+            p[q] = excl.plus(run);
         }
     }
 
-    // S_j from the DST output area: even j -> buf[j/2], odd j -> odd area
-    static __device__ __forceinline__ cpx<T> s_at(const cpx<T> *buf, int j)
-    {
-        return (j & 1) ? buf[odd_pos(j >> 1)] : buf[j >> 1];
-    }
-
     template <int RM, int PP>
-    static __device__ __forceinline__ void mid_pass(cpx<T> *x, cpx<T> *buf, const typename Prec<T>::C *W, int g)
+    static __device__ __forceinline__ void mid_pass(cpx<T> *x, cpx<T> *buf, const C *W, int g)
     {
         if constexpr (RM > 1) {
             constexpr int NB = N / RM, PER = E / RM;
@@ -289,7 +353,7 @@ template <typename T, int N> struct Fused {
                 const int i = g + q * G, k = i & (PP - 1);
 #pragma unroll
                 for (int m = 0; m < RM; ++m) {
-                    cpx<T> v = buf[i + m * NB];
+                    cpx<T> v = buf[pad(i + m * NB)];
                     if (m) v = PR::mul(v, PR::ld(&W[m * k * (N / (PP * RM))]));
                     x[q * RM + m] = v;
                 }
@@ -298,73 +362,171 @@ template <typename T, int N> struct Fused {
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 const int i = g + q * G, k = i & (PP - 1);
-                DFT<T, RM>::template run<1>(x + q * RM);
+                DFTI<T, RM>::run(x + q * RM);
                 const int base = (i - k) * RM + k;
 #pragma unroll
-                for (int m = 0; m < RM; ++m) buf[base + m * PP] = x[q * RM + m];
+                for (int m = 0; m < RM; ++m) buf[pad(base + m * PP)] = x[q * RM + DFTI<T, RM>::operm(m)];
             }
             __syncthreads();
         }
     }
 
-    // x (first-pass layout, values f_j at idx(g, e)) -> DST output in buf (even/odd areas)
-    static __device__ __forceinline__ void dst(cpx<T> *x, cpx<T> *buf, const Tables<T> &tb, int g, ScanVal<T> *wtot)
+    // S (E/odd layout in buf), optionally times K_T, at the first-pass indices -> DST -> E/odd layout
+    static __device__ __forceinline__ void dst(cpx<T> *x, cpx<T> *buf, const Tables<T> &tb, int g, Carry<T> *wtot,
+                                               bool kinetic)
     {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j = idx(g, e);
+            cpx<T> v = buf[s_pos(j)];
+            if (kinetic) v = PR::mul(v, PR::ld(&tb.KT[j]));
+            x[e] = v;
+        }
+        __syncthreads();
         pre(x, g, tb.sinpre);
-        // first pass (radix R, no twiddles): butterfly b -> buf[b R + m]
+        // first pass (radix R, no twiddles): butterfly b -> [b R + k]
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            DFT<T, R>::template run<1>(x + t * R);
-            const int b = (t == 0) ? (g == 0 ? 0 : g) : (g == 0 ? NR / 2 : NR - g);
+            DR::run(x + t * R);
+            const int b = b_of(g, t);
 #pragma unroll
-            for (int m = 0; m < R; ++m) buf[b * R + m] = x[t * R + m];
+            for (int k = 0; k < R; ++k) buf[pad(b * R + k)] = x[t * R + DR::operm(k)];
         }
         __syncthreads();
         mid_pass<P::M1, R>(x, buf, tb.W, g);
         mid_pass<P::M2, R * P::M1>(x, buf, tb.W, g);
-        // last pass (radix R, P = N/R): inputs buf[b + m NR], twiddle W^(m b), outputs stay in registers
+        // last pass (radix R, stride N/R): inputs [b + m NR], twiddle W^(m b)
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            const int b = (t == 0) ? (g == 0 ? 0 : g) : (g == 0 ? NR / 2 : NR - g);
+            const int b = b_of(g, t);
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                cpx<T> v = buf[b + m * NR];
+                cpx<T> v = buf[pad(b + m * NR)];
                 if (m) v = PR::mul(v, PR::ld(&tb.W[m * b]));
                 x[t * R + m] = v;
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int t = 0; t < 2; ++t) DFT<T, R>::template run<1>(x + t * R);
+        for (int t = 0; t < 2; ++t) DR::run(x + t * R);
         post(x, g, buf);
         __syncthreads();
         scan(buf, g, wtot);
         __syncthreads();
     }
+};
 
-    // x <- K_V x for (colour, l) at T^3
-    static __device__ __forceinline__ void space_kernel(cpx<T> *x, const Tables<T> &tb, int g, int c, int l, T er, T ei,
-                                                        T dr)
+// ------------------------------------------------------------------------------------------------
+// pointwise work on the E/odd layout: thread g visits k = g, g + G, ... < N/2 and the two elements
+// S_{2k} (at [k]) and S_{2k+1} (at odd_pos(k))
+// ------------------------------------------------------------------------------------------------
+template <typename T, int N> struct Pointwise {
+    using K = Fused<T, N>;
+    using PR = Prec<T>;
+    using C = typename Prec<T>::C;
+    static constexpr int G = K::G;
+
+    static __device__ __forceinline__ C stat(const Tables<T> &tb, const C *tab, int c, int l, int j, bool full)
     {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int j = idx(g, e);
-            const T r = (T)j * dr;
-            x[e] = PR::mul(x[e], static_factor<T>(tb, N, c, l, j)) * dyn_factor(er, ei, r * r);
-        }
+        if (l < LTAB) return PR::ld(&tab[((size_t)c * LTAB + l) * N + j]);
+        if (j == 0) return PR::from_double(0.0, 0.0);
+        return static_far<T>(tb.coul[c], tb.M, tb.dt, l, j * tb.dr, full ? 2.0 : 1.0);
     }
 
-    static __device__ __forceinline__ double norm2(const cpx<T> *x, double *red, double dr)
+    // mode 0: x <- stat1 dyn_b x (the first half-step of a trajectory)
+    // mode 1: x <- stat2 dyn_a dyn_b x; returns sum exp(2 er_a r^2) |x_old|^2 (end-of-step norm / dr)
+    // mode 2: x <- stat1 dyn_a x; returns sum |x_new|^2
+    // dyn = exp((er + i ei) r^2) with er, ei already multiplied by T^3; eip = ei / pi
+    static __device__ double factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode, T er_a, T eip_a,
+                                    T er_b, T eip_b, double *red)
     {
+        const C *tab = (mode == 1) ? tb.statV2 : tb.statV;
+        const T ers = (mode == 0 ? (T)0 : er_a) + (mode == 2 ? (T)0 : er_b);
+        const T eps = (mode == 0 ? (T)0 : eip_a) + (mode == 2 ? (T)0 : eip_b);
+        const T del = er_a - er_b;
+        const T dr = (T)tb.dr;
         SqAcc<T> acc;
+#pragma unroll 2
+        for (int k = g; k < N / 2; k += G) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc.add(x[e]);
-        return slot_norm<T, G>(acc, red) * dr;
+            for (int par = 0; par < 2; ++par) {
+                const int j = 2 * k + par;
+                const int p = par ? K::odd_pos(k) : k;
+                const T r = (T)j * dr, r2 = r * r;
+                const T mag = k_exp(ers * r2);
+                T s, co;
+                k_sincospi(eps * r2, &s, &co);
+                cpx<T> v = buf[p];
+                if (mode == 1) {
+                    // exp(2 er_a r^2) = mag * exp((er_a - er_b) r^2), the second factor ~ 1 + 1e-4
+                    const T z = del * r2;
+                    acc.add_w(v, mag * ((T)1 + z * ((T)1 + z * ((T)0.5 + z * (T)(1.0 / 6.0)))));
+                }
+                v = PR::mul(v, stat(tb, tab, c, l, j, mode == 1)) * mk(mag * co, mag * s);
+                if (mode == 2) acc.add_w(v, (T)1);
+                buf[p] = v;
+            }
+        }
+        if (mode == 0) return 0.0;
+        return slot_norm<T, G>(acc, red);
+    }
+
+    static __device__ cpx<double> to_d(const typename Prec<double>::C &a) { return a; }
+    static __device__ cpx<double> to_d(const typename Prec<float>::C &a)
+    {
+        return mk((double)a.rh + (double)a.rl, (double)a.ih + (double)a.il);
+    }
+
+    // A jump after the factor of mode 1 (more steps follow) or mode 2 (after the last step).
+    // Returns sum r^2 |end-of-step state|^2 (/ dr); with mode 1 the end-of-step state is
+    // exp(-er_b r^2) times the stored one.  With mode 1 it also turns the start half-step already
+    // applied from (c, l) into (c2, l2): x <- conj(stat1(c,l)) stat1(c2,l2) exp(d_er r^2 + i d_ei r^2) x.
+    static __device__ double jump_turn(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int c2, int l2,
+                                       bool after_last, double er_b, double d_er, double d_ei, double *red)
+    {
+        double s = 0.0;
+        for (int k = g; k < N / 2; k += G) {
+            for (int par = 0; par < 2; ++par) {
+                const int j = 2 * k + par;
+                const int p = par ? K::odd_pos(k) : k;
+                const double r = j * tb.dr, r2 = r * r;
+                const cpx<T> v = buf[p];
+                const double a2 = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                if (after_last) {
+                    s += r2 * a2;
+                } else {
+                    s += r2 * exp(-2.0 * er_b * r2) * a2;
+                    const cpx<double> a = to_d(stat(tb, tb.statV, c, l, j, false));
+                    const cpx<double> b = to_d(stat(tb, tb.statV, c2, l2, j, false));
+                    double sn, cs;
+                    sincos(d_ei * r2, &sn, &cs);
+                    const double m = exp(d_er * r2);
+                    const cpx<double> f = mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x) * mk(m * cs, m * sn);
+                    const cpx<double> vd = mk((double)v.x, (double)v.y) * f;
+                    buf[p] = mk<T>((T)vd.x, (T)vd.y);
+                }
+            }
+        }
+        return slot_sum<G>(s, red);
+    }
+
+    // x <- x * r_j * f
+    static __device__ void scale_r(cpx<T> *buf, const Tables<T> &tb, int g, double f)
+    {
+        for (int k = g; k < N / 2; k += G) {
+            for (int par = 0; par < 2; ++par) {
+                const int j = 2 * k + par;
+                const int p = par ? K::odd_pos(k) : k;
+                const double m = j * tb.dr * f;
+                const cpx<T> v = buf[p];
+                buf[p] = mk<T>((T)((double)v.x * m), (T)((double)v.y * m));
+            }
+        }
     }
 };
 
-// one thread per CTA takes trajectories from the counter; r0 < p_NoJump and r0 > r_max are resolved
-// here without evolving
+// One thread per CTA takes trajectories from the counter; r0 < p_NoJump and r0 > r_max are resolved
+// here without evolving.
 template <typename T>
 __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
 {
@@ -405,17 +567,25 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
     }
 }
 
+template <typename T, int N> struct FusedBounds {
+    static constexpr int G = FusedPlan<N>::G;
+    // FP32: at least 512 resident threads per SM (<= 128 registers); FP64 holds twice the state
+    static constexpr int MB = 512 / G > 32 ? 32 : (512 / G > 0 ? 512 / G : 1);
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? MB : 1;
+};
+
 template <typename T, int N>
-__global__ void __launch_bounds__(FusedPlan<N>::G) fused_kernel(Tables<T> tb, LaunchArgs a)
+__global__ void __launch_bounds__(FusedPlan<N>::G, FusedBounds<T, N>::MIN_BLOCKS) fused_kernel(Tables<T> tb, LaunchArgs a)
 {
     using K = Fused<T, N>;
-    constexpr int R = K::R, G = K::G, E = K::E;
+    using PW = Pointwise<T, N>;
+    constexpr int G = K::G, E = K::E;
+    constexpr double INV_PI = 0.31830988618379067154;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T> *buf = reinterpret_cast<cpx<T> *>(smem_raw);
-    ScanVal<T> *wtot = reinterpret_cast<ScanVal<T> *>(buf + FusedPlan<N>::BUF);
+    Carry<T> *wtot = reinterpret_cast<Carry<T> *>(buf + FusedPlan<N>::BUF);
     double *red = reinterpret_cast<double *>(wtot + (G / 32 + 1));
     __shared__ int s_traj;
-    (void)R;
 
     const int g = threadIdx.x;
     const double dr = tb.dr;
@@ -432,36 +602,33 @@ __global__ void __launch_bounds__(FusedPlan<N>::G) fused_kernel(Tables<T> tb, La
         const MediumDev md = tb.media[d.medium];
         int l = tb.spec_l[d.spec], c = tb.spec_color[d.spec];
         const double *ic = tb.ic + (size_t)d.spec * N;
-#pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = mk<T>((T)ic[K::idx(g, e)], (T)0);
-
+        for (int k = g; k < N / 2; k += G) {
+            buf[k] = mk<T>((T)ic[2 * k], (T)0);
+            buf[K::odd_pos(k)] = mk<T>((T)ic[2 * k + 1], (T)0);
+        }
         uint32_t kdraw = 0;
         Draws dw = draws(d.seed, 0u);
         const double r0 = a.nojump ? 0.0 : dw.r;
         double thr = a.nojump ? -1.0 : dw.r;
         int nj = 0, flags = 0, fj = -1, ended = 0, executed = 0;
         const int ns = d.n_steps;
+        double T3b = md.A / md.tau0;
+        if (ns > 0) {
+            __syncthreads();
+            PW::factor(buf, tb, g, c, l, 0, (T)0, (T)0, (T)(md.er[c] * T3b), (T)(md.ei[c] * T3b * INV_PI), red);
+        }
 
         for (int n = 0; n < ns; ++n) {
-            const double T3 = md.A / (md.tau0 + (double)n * md.dtau);
-            const T er = (T)(md.er[c] * T3), ei = (T)(md.ei[c] * T3);
-            K::space_kernel(x, tb, g, c, l, er, ei, (T)dr);
-            K::dst(x, buf, tb, g, wtot);
-            // kinetic step on the spectrum, back to registers
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int j = K::idx(g, e);
-                x[e] = Prec<T>::mul(K::s_at(buf, j), Prec<T>::ld(&tb.KT[j]));
-            }
+            const double T3a = T3b;
+            const bool last = (n + 1 == ns);
+            T3b = md.A / (md.tau0 + (double)(n + 1) * md.dtau);
             __syncthreads();
-            K::dst(x, buf, tb, g, wtot);
-#pragma unroll
-            for (int e = 0; e < E; ++e) x[e] = K::s_at(buf, K::idx(g, e));
-            __syncthreads();                           // buf is free for the next step
-            K::space_kernel(x, tb, g, c, l, er, ei, (T)dr);
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) K::dst(x, buf, tb, g, wtot, h == 1);
             executed = n + 1;
-
-            const double n2 = K::norm2(x, red, dr);
+            const T er_a = (T)(md.er[c] * T3a), eip_a = (T)(md.ei[c] * T3a * INV_PI);
+            const T er_b = last ? (T)0 : (T)(md.er[c] * T3b), eip_b = last ? (T)0 : (T)(md.ei[c] * T3b * INV_PI);
+            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, er_a, eip_a, er_b, eip_b, red) * dr;
             if (!isfinite(n2)) {
                 flags |= QTRAJ_F_NONFINITE;
                 ended = 1;
@@ -485,21 +652,16 @@ __global__ void __launch_bounds__(FusedPlan<N>::G) fused_kernel(Tables<T> tb, La
                         ended = 1;
                         break;
                     }
-                    // psi <- r psi / ||r psi||
-                    double s = 0.0;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const double rj = K::idx(g, e) * dr;
-                        const double xr = (double)x[e].x * rj, xi = (double)x[e].y * rj;
-                        s += xr * xr + xi * xi;
-                    }
-                    s = slot_sum<G>(s, red) * dr;
-                    const double inv = 1.0 / sqrt(s);
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const double f = K::idx(g, e) * dr * inv;
-                        x[e] = mk<T>((T)((double)x[e].x * f), (T)((double)x[e].y * f));
-                    }
+                    // r times the end-of-step state, renormalised; the start half-step already applied
+                    // is turned into the new colour's and l's
+                    __syncthreads();
+                    const double erb = (double)er_b;
+                    const double d_er = last ? 0.0 : (md.er[c_new] - md.er[c]) * T3b;
+                    const double d_ei = last ? 0.0 : (md.ei[c_new] - md.ei[c]) * T3b;
+                    const double s = PW::jump_turn(buf, tb, g, c, l, c_new, l_new, last, erb, d_er, d_ei, red) * dr;
+                    const double f = 1.0 / sqrt(s);
+                    __syncthreads();
+                    PW::scale_r(buf, tb, g, f);
                     l = l_new; c = c_new; ++nj;
                     ++kdraw;
                     dw = draws(d.seed, kdraw);
@@ -507,36 +669,41 @@ __global__ void __launch_bounds__(FusedPlan<N>::G) fused_kernel(Tables<T> tb, La
                 }
             }
         }
+        __syncthreads();
 
         // observables (FP64)
-        const double n2 = K::norm2(x, red, dr);
+        double acc = 0.0;
+        for (int k = g; k < N / 2; k += G) {
+            const cpx<T> a0 = buf[k], a1 = buf[K::odd_pos(k)];
+            acc += (double)a0.x * a0.x + (double)a0.y * a0.y + (double)a1.x * a1.x + (double)a1.y * a1.y;
+        }
+        const double n2 = slot_sum<G>(acc, red) * dr;
         double ovr[NBASIS], ovi[NBASIS];
-#pragma unroll
-        for (int s = 0; s < NBASIS; ++s) { ovr[s] = 0.0; ovi[s] = 0.0; }
         const int basis_l[NBASIS] = {0, 0, 1, 0, 1, 2};
-        if (!ended && c == 0) {
-#pragma unroll 1
-            for (int s = 0; s < NBASIS; ++s) {
-                if (basis_l[s] != l) continue;
-                const double *phi = tb.eig + (size_t)s * N;
-                double pr = 0.0, pi = 0.0;
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const double f = phi[K::idx(g, e)];
-                    pr += f * (double)x[e].x;
-                    pi += f * (double)x[e].y;
-                }
-                ovr[s] = slot_sum<G>(pr, red) * dr;
-                ovi[s] = slot_sum<G>(pi, red) * dr;
+        for (int s = 0; s < NBASIS; ++s) {
+            ovr[s] = 0.0;
+            ovi[s] = 0.0;
+            if (ended || c != 0 || basis_l[s] != l) continue;
+            const double *phi = tb.eig + (size_t)s * N;
+            double pr = 0.0, pi = 0.0;
+            for (int k = g; k < N / 2; k += G) {
+                const cpx<T> a0 = buf[k], a1 = buf[K::odd_pos(k)];
+                const double f0 = phi[2 * k], f1 = phi[2 * k + 1];
+                pr += f0 * (double)a0.x + f1 * (double)a1.x;
+                pi += f0 * (double)a0.y + f1 * (double)a1.y;
             }
+            ovr[s] = slot_sum<G>(pr, red) * dr;
+            ovi[s] = slot_sum<G>(pi, red) * dr;
         }
         if (a.states) {
             double *st = a.states + (size_t)t * N * 2;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int j = K::idx(g, e);
-                st[2 * j] = (double)x[e].x;
-                st[2 * j + 1] = (double)x[e].y;
+            for (int k = g; k < N / 2; k += G) {
+                const cpx<T> a0 = buf[k], a1 = buf[K::odd_pos(k)];
+                st[4 * k] = (double)a0.x;
+                st[4 * k + 1] = (double)a0.y;
+                st[4 * k + 2] = (double)a1.x;
+                st[4 * k + 3] = (double)a1.y;
             }
         }
         if (g == 0) {
@@ -573,7 +740,7 @@ __global__ void __launch_bounds__(FusedPlan<N>::G) fused_kernel(Tables<T> tb, La
 // shared-memory bytes of one CTA
 template <typename T, int N> constexpr int fused_smem_bytes()
 {
-    return FusedPlan<N>::BUF * (int)sizeof(cpx<T>) + (FusedPlan<N>::G / 32 + 1) * (int)sizeof(ScanVal<T>) +
+    return FusedPlan<N>::BUF * (int)sizeof(cpx<T>) + (FusedPlan<N>::G / 32 + 1) * (int)sizeof(Carry<T>) +
            (FusedPlan<N>::G / 32 + 1) * 8 + 16;
 }
 

@@ -279,6 +279,7 @@ template <typename T> struct Tables {
     const C *KT;                       // N kinetic factors exp(-i T_kin(p_k) dt) * 2/N, k = 0..N-1
     const typename Prec<T>::Rl *sinpre; // N values sin(pi j / N)
     const C *statV;                    // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
+    const C *statV2;                   // [2][LTAB][N] the same over a full step, exp(-i (...) dt)
     const double *eig;     // [NBASIS][N] Coulomb basis, discretely normalised
     const double *ic;      // [n_spec][N] initial states, discretely normalised
     const double *ov0;     // [n_spec][NBASIS][2] initial overlaps
