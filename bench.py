@@ -140,7 +140,8 @@ def run_ours(args):
     specs = [qtraj.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits]
     media = [qtraj.medium(m.T0, m.tau0, m.Tf, m.kappa_hat, m.gamma_hat) for m in w.media]
     prec = qtraj.FP32 if args.precision == "fp32" else qtraj.FP64
-    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=qtraj.FUSED))
+    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=qtraj.FUSED,
+                                    variant=args.variant))
     n_slices = total // B
 
     # every rank owns disjoint trajectory ids: step i of rank r takes slice (i*world + r) mod n_slices
@@ -237,7 +238,8 @@ def run_ours(args):
                       "d2h_bytes_per_step": int(B * qtraj.OBS_DTYPE.itemsize + 4)},
               "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
               "kernel": {"threads_per_traj": kinfo.threads_per_traj, "ctas_per_sm": kinfo.ctas_per_sm,
-                         "smem_bytes": kinfo.smem_bytes, "regs": kinfo.regs_per_thread, "radix": kinfo.radix}}
+                         "smem_bytes": kinfo.smem_bytes, "regs": kinfo.regs_per_thread, "radix": kinfo.radix,
+                         "variant": args.variant}}
 
     if rank == 0 and not args.no_compare:
         result["plain_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.PLAIN, args.compare_batch)
@@ -340,7 +342,8 @@ def run_profile_case(args):
     media = [qtraj.medium(m.T0, m.tau0, m.T0 * (m.tau0 / tau_end) ** (1 / 3) * (1 + 1e-9), m.kappa_hat, m.gamma_hat)
              for m in w.media]
     prec = qtraj.FP32 if args.precision == "fp32" else qtraj.FP64
-    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=qtraj.FUSED, use_rmin=0))
+    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=qtraj.FUSED, use_rmin=0,
+                                    variant=args.variant))
     specs = [qtraj.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits]
     eng.init(specs, B, spec_idx=w.init_idx[:B])
     for _ in range(2):
@@ -361,11 +364,12 @@ def main():
     ap.add_argument("--batch", type=int, default=9216, help="trajectories per bench step (multiple of 18)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--compare-batch", type=int, default=256)
+    ap.add_argument("--variant", type=int, default=0, help="fused kernel occupancy variant (0 or 1)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
-    ap.add_argument("--profile-steps", type=int, default=200)
+    ap.add_argument("--profile-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.profile_case:
         from paper_2107_06147_gb300 import build

@@ -270,6 +270,7 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     if (p.precision != QTRAJ_FP64 && p.precision != QTRAJ_FP32) return fail(QTRAJ_EINVAL, "unknown precision");
     if (p.form != QTRAJ_FUSED && p.form != QTRAJ_PLAIN) return fail(QTRAJ_EINVAL, "unknown form");
     if (p.form == QTRAJ_PLAIN && p.precision != QTRAJ_FP64) return fail(QTRAJ_EINVAL, "the plain form is FP64 only");
+    if (p.variant != 0 && p.variant != 1) return fail(QTRAJ_EINVAL, "variant must be 0 or 1");
     if (p.form == QTRAJ_FUSED && p.precision == QTRAJ_FP64 && N > 8192)
         return fail(QTRAJ_EINVAL, "the fused FP64 form supports N <= 8192");
 
@@ -540,21 +541,21 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
         if (c->p.precision == QTRAJ_FP32) {
             const Tables<float> tb = tables<float>(c);
             if (n_groups > 0) {
-                CK(fused_launch_f32(N, tb, ga, c->sm_count, 0, s, &fi, false));
+                CK(fused_launch_f32(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
                 ++c->launches;
                 CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
             }
             CK(cudaEventRecord(c->ev1, s));
-            CK(fused_launch_f32(N, tb, ma, c->sm_count, 0, s, &fi, false));
+            CK(fused_launch_f32(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
         } else {
             const Tables<double> tb = tables<double>(c);
             if (n_groups > 0) {
-                CK(fused_launch_f64(N, tb, ga, c->sm_count, 0, s, &fi, false));
+                CK(fused_launch_f64(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
                 ++c->launches;
                 CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
             }
             CK(cudaEventRecord(c->ev1, s));
-            CK(fused_launch_f64(N, tb, ma, c->sm_count, 0, s, &fi, false));
+            CK(fused_launch_f64(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
         }
         ++c->launches;
     }
@@ -643,8 +644,8 @@ qtraj_status qtraj_kernel_info_get(const qtraj_ctx *c, qtraj_kernel_info *out)
     if (c->p.form == QTRAJ_PLAIN) return QTRAJ_OK;
     FusedInfo fi{};
     LaunchArgs none{};
-    if (c->p.precision == QTRAJ_FP32) CK(fused_launch_f32(c->N, tables<float>(c), none, c->sm_count, 0, nullptr, &fi, true));
-    else CK(fused_launch_f64(c->N, tables<double>(c), none, c->sm_count, 0, nullptr, &fi, true));
+    if (c->p.precision == QTRAJ_FP32) CK(fused_launch_f32(c->N, tables<float>(c), none, c->sm_count, 0, nullptr, &fi, true, c->p.variant));
+    else CK(fused_launch_f64(c->N, tables<double>(c), none, c->sm_count, 0, nullptr, &fi, true, c->p.variant));
     out->threads_per_traj = fi.G;
     out->ctas_per_sm = fi.ctas_per_sm;
     out->smem_bytes = fi.smem;

@@ -102,16 +102,22 @@ template <> struct SqAcc<double> {
     __device__ __forceinline__ double value() const { return v; }
 };
 
-// compensated complex value for the scan's carries between threads
+// compensated complex value for the scan's carries between threads.  Chunk totals use cascaded
+// summation (the TwoSum error terms are collected separately); carries between threads are
+// double-float additions.
 template <typename T> struct Carry;
 template <> struct Carry<float> {
     DF re{0.f, 0.f}, im{0.f, 0.f};
-    __device__ __forceinline__ void add(cpx<float> a) { re = df_add_f(re, a.x, 0.f); im = df_add_f(im, a.y, 0.f); }
-    __device__ __forceinline__ void add(const Carry &o) { re = df_add(re, o.re); im = df_add(im, o.im); }
-    __device__ __forceinline__ cpx<float> plus(cpx<float> a) const   // (this + a) rounded once
+    __device__ __forceinline__ void add(cpx<float> a)
     {
-        const DF r = df_add_f(re, a.x, 0.f), i = df_add_f(im, a.y, 0.f);
-        return mk(r.hi + r.lo, i.hi + i.lo);
+        const DF r = two_sum(re.hi, a.x), i = two_sum(im.hi, a.y);
+        re = DF{r.hi, re.lo + r.lo};
+        im = DF{i.hi, im.lo + i.lo};
+    }
+    __device__ __forceinline__ void add(const Carry &o) { re = df_add(re, o.re); im = df_add(im, o.im); }
+    __device__ __forceinline__ cpx<float> plus(cpx<float> a) const   // this + a, one rounding of the sum
+    {
+        return mk((re.hi + a.x) + re.lo, (im.hi + a.y) + im.lo);
     }
     __device__ __forceinline__ Carry shfl_up(unsigned mask, int off, int w) const
     {
@@ -436,15 +442,18 @@ template <typename T, int N> struct Pointwise {
     // mode 0: x <- stat1 dyn_b x (the first half-step of a trajectory)
     // mode 1: x <- stat2 dyn_a dyn_b x; returns sum exp(2 er_a r^2) |x_old|^2 (end-of-step norm / dr)
     // mode 2: x <- stat1 dyn_a x; returns sum |x_new|^2
-    // dyn = exp((er + i ei) r^2) with er, ei already multiplied by T^3; eip = ei / pi
-    static __device__ double factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode, T er_a, T eip_a,
-                                    T er_b, T eip_b, double *red)
+    // dyn = exp((er + i ei) r^2) with er, ei already multiplied by T^3.  The coefficients enter times
+    // dr^2 and the phase divided by pi, rounded once per call, and multiply the exact j twice: no
+    // rounding that repeats identically every step enters the arguments.
+    static __device__ double factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode, double er_a,
+                                    double ei_a, double er_b, double ei_b, double *red)
     {
+        constexpr double INV_PI = 0.31830988618379067154;
         const C *tab = (mode == 1) ? tb.statV2 : tb.statV;
-        const T ers = (mode == 0 ? (T)0 : er_a) + (mode == 2 ? (T)0 : er_b);
-        const T eps = (mode == 0 ? (T)0 : eip_a) + (mode == 2 ? (T)0 : eip_b);
-        const T del = er_a - er_b;
-        const T dr = (T)tb.dr;
+        const double dr2 = tb.dr * tb.dr;
+        const double ers = (mode == 0 ? 0.0 : er_a) + (mode == 2 ? 0.0 : er_b);
+        const double eis = (mode == 0 ? 0.0 : ei_a) + (mode == 2 ? 0.0 : ei_b);
+        const T A = (T)(ers * dr2), B = (T)(eis * dr2 * INV_PI), D = (T)((er_a - er_b) * dr2);
         SqAcc<T> acc;
 #pragma unroll 2
         for (int k = g; k < N / 2; k += G) {
@@ -452,14 +461,14 @@ template <typename T, int N> struct Pointwise {
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
                 const int p = par ? K::odd_pos(k) : k;
-                const T r = (T)j * dr, r2 = r * r;
-                const T mag = k_exp(ers * r2);
+                const T fj = (T)j;
+                const T mag = k_exp((A * fj) * fj);
                 T s, co;
-                k_sincospi(eps * r2, &s, &co);
+                k_sincospi((B * fj) * fj, &s, &co);
                 cpx<T> v = buf[p];
                 if (mode == 1) {
                     // exp(2 er_a r^2) = mag * exp((er_a - er_b) r^2), the second factor ~ 1 + 1e-4
-                    const T z = del * r2;
+                    const T z = (D * fj) * fj;
                     acc.add_w(v, mag * ((T)1 + z * ((T)1 + z * ((T)0.5 + z * (T)(1.0 / 6.0)))));
                 }
                 v = PR::mul(v, stat(tb, tab, c, l, j, mode == 1)) * mk(mag * co, mag * s);
@@ -567,20 +576,22 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
     }
 }
 
-template <typename T, int N> struct FusedBounds {
+// Occupancy target of a kernel variant: variant 0 asks for 512 resident threads per SM in FP32
+// (<= 128 registers), variant 1 for 640 (<= 102 registers, at the price of some spills).  FP64
+// holds twice the state and takes what the compiler needs.
+template <typename T, int N, int V> struct FusedBounds {
     static constexpr int G = FusedPlan<N>::G;
-    // FP32: at least 512 resident threads per SM (<= 128 registers); FP64 holds twice the state
-    static constexpr int MB = 512 / G > 32 ? 32 : (512 / G > 0 ? 512 / G : 1);
+    static constexpr int THREADS = V == 0 ? 512 : 640;
+    static constexpr int MB = THREADS / G > 32 ? 32 : (THREADS / G > 0 ? THREADS / G : 1);
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? MB : 1;
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(FusedPlan<N>::G, FusedBounds<T, N>::MIN_BLOCKS) fused_kernel(Tables<T> tb, LaunchArgs a)
+template <typename T, int N, int V>
+__global__ void __launch_bounds__(FusedPlan<N>::G, (FusedBounds<T, N, V>::MIN_BLOCKS)) fused_kernel(Tables<T> tb, LaunchArgs a)
 {
     using K = Fused<T, N>;
     using PW = Pointwise<T, N>;
     constexpr int G = K::G, E = K::E;
-    constexpr double INV_PI = 0.31830988618379067154;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T> *buf = reinterpret_cast<cpx<T> *>(smem_raw);
     Carry<T> *wtot = reinterpret_cast<Carry<T> *>(buf + FusedPlan<N>::BUF);
@@ -615,7 +626,7 @@ __global__ void __launch_bounds__(FusedPlan<N>::G, FusedBounds<T, N>::MIN_BLOCKS
         double T3b = md.A / md.tau0;
         if (ns > 0) {
             __syncthreads();
-            PW::factor(buf, tb, g, c, l, 0, (T)0, (T)0, (T)(md.er[c] * T3b), (T)(md.ei[c] * T3b * INV_PI), red);
+            PW::factor(buf, tb, g, c, l, 0, 0.0, 0.0, md.er[c] * T3b, md.ei[c] * T3b, red);
         }
 
         for (int n = 0; n < ns; ++n) {
@@ -626,9 +637,9 @@ __global__ void __launch_bounds__(FusedPlan<N>::G, FusedBounds<T, N>::MIN_BLOCKS
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) K::dst(x, buf, tb, g, wtot, h == 1);
             executed = n + 1;
-            const T er_a = (T)(md.er[c] * T3a), eip_a = (T)(md.ei[c] * T3a * INV_PI);
-            const T er_b = last ? (T)0 : (T)(md.er[c] * T3b), eip_b = last ? (T)0 : (T)(md.ei[c] * T3b * INV_PI);
-            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, er_a, eip_a, er_b, eip_b, red) * dr;
+            const double er_a = md.er[c] * T3a, ei_a = md.ei[c] * T3a;
+            const double er_b = last ? 0.0 : md.er[c] * T3b, ei_b = last ? 0.0 : md.ei[c] * T3b;
+            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, er_a, ei_a, er_b, ei_b, red) * dr;
             if (!isfinite(n2)) {
                 flags |= QTRAJ_F_NONFINITE;
                 ended = 1;
@@ -655,7 +666,7 @@ __global__ void __launch_bounds__(FusedPlan<N>::G, FusedBounds<T, N>::MIN_BLOCKS
                     // r times the end-of-step state, renormalised; the start half-step already applied
                     // is turned into the new colour's and l's
                     __syncthreads();
-                    const double erb = (double)er_b;
+                    const double erb = er_b;
                     const double d_er = last ? 0.0 : (md.er[c_new] - md.er[c]) * T3b;
                     const double d_ei = last ? 0.0 : (md.ei[c_new] - md.ei[c]) * T3b;
                     const double s = PW::jump_turn(buf, tb, g, c, l, c_new, l_new, last, erb, d_er, d_ei, red) * dr;

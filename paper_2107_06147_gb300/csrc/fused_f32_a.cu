@@ -4,13 +4,13 @@
 
 namespace qt {
 cudaError_t fused_launch_f32_b(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only);
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant);
 namespace {
-template <int N>
+template <int N, int V>
 cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s, FusedInfo *info,
                bool query_only)
 {
-    auto k = fused_kernel<float, N>;
+    auto k = fused_kernel<float, N, V>;
     constexpr int G = FusedPlan<N>::G;
     constexpr int smem = fused_smem_bytes<float, N>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -39,17 +39,17 @@ cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int m
 } // namespace
 
 cudaError_t fused_launch_f32(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only)
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
     switch (N) {
-    case 16: return go<16>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 32: return go<32>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 64: return go<64>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 128: return go<128>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 256: return go<256>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 512: return go<512>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 1024: return go<1024>(tb, a, sm_count, max_ctas, s, info, query_only);
-    default: return fused_launch_f32_b(N, tb, a, sm_count, max_ctas, s, info, query_only);
+    case 16: return go<16, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 32: return go<32, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 64: return go<64, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 128: return go<128, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 256: return go<256, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 512: return go<512, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 1024: return go<1024, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    default: return fused_launch_f32_b(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);
     }
 }
 

@@ -4,13 +4,13 @@
 
 namespace qt {
 cudaError_t fused_launch_f32_c(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only);
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant);
 namespace {
-template <int N>
+template <int N, int V>
 cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s, FusedInfo *info,
                bool query_only)
 {
-    auto k = fused_kernel<float, N>;
+    auto k = fused_kernel<float, N, V>;
     constexpr int G = FusedPlan<N>::G;
     constexpr int smem = fused_smem_bytes<float, N>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -39,12 +39,14 @@ cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int m
 } // namespace
 
 cudaError_t fused_launch_f32_b(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only)
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
     switch (N) {
-    case 2048: return go<2048>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 4096: return go<4096>(tb, a, sm_count, max_ctas, s, info, query_only);
-    default: return fused_launch_f32_c(N, tb, a, sm_count, max_ctas, s, info, query_only);
+    case 2048: return variant == 1 ? go<2048, 1>(tb, a, sm_count, max_ctas, s, info, query_only)
+                          : go<2048, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 4096: return variant == 1 ? go<4096, 1>(tb, a, sm_count, max_ctas, s, info, query_only)
+                          : go<4096, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    default: return fused_launch_f32_c(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);
     }
 }
 

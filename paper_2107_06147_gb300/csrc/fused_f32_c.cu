@@ -4,11 +4,11 @@
 
 namespace qt {
 namespace {
-template <int N>
+template <int N, int V>
 cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s, FusedInfo *info,
                bool query_only)
 {
-    auto k = fused_kernel<float, N>;
+    auto k = fused_kernel<float, N, V>;
     constexpr int G = FusedPlan<N>::G;
     constexpr int smem = fused_smem_bytes<float, N>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -37,11 +37,11 @@ cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int m
 } // namespace
 
 cudaError_t fused_launch_f32_c(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only)
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
     switch (N) {
-    case 8192: return go<8192>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 16384: return go<16384>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 8192: return go<8192, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 16384: return go<16384, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -4,13 +4,13 @@
 
 namespace qt {
 cudaError_t fused_launch_f64_c(int N, const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only);
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant);
 namespace {
-template <int N>
+template <int N, int V>
 cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s, FusedInfo *info,
                bool query_only)
 {
-    auto k = fused_kernel<double, N>;
+    auto k = fused_kernel<double, N, V>;
     constexpr int G = FusedPlan<N>::G;
     constexpr int smem = fused_smem_bytes<double, N>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -39,12 +39,12 @@ cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int 
 } // namespace
 
 cudaError_t fused_launch_f64_b(int N, const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only)
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
     switch (N) {
-    case 2048: return go<2048>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 4096: return go<4096>(tb, a, sm_count, max_ctas, s, info, query_only);
-    default: return fused_launch_f64_c(N, tb, a, sm_count, max_ctas, s, info, query_only);
+    case 2048: return go<2048, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 4096: return go<4096, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    default: return fused_launch_f64_c(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);
     }
 }
 

@@ -4,11 +4,11 @@
 
 namespace qt {
 namespace {
-template <int N>
+template <int N, int V>
 cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s, FusedInfo *info,
                bool query_only)
 {
-    auto k = fused_kernel<double, N>;
+    auto k = fused_kernel<double, N, V>;
     constexpr int G = FusedPlan<N>::G;
     constexpr int smem = fused_smem_bytes<double, N>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -37,10 +37,10 @@ cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int 
 } // namespace
 
 cudaError_t fused_launch_f64_c(int N, const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
-                             cudaStream_t s, FusedInfo *info, bool query_only)
+                             cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
     switch (N) {
-    case 8192: return go<8192>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 8192: return go<8192, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -31,7 +31,7 @@ class QtrajError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int), ("max_jumps", C.c_int),
                 ("r_max", C.c_double), ("l_cap", C.c_int), ("use_rmin", C.c_int), ("precision", C.c_int),
-                ("form", C.c_int), ("save_states", C.c_int)]
+                ("form", C.c_int), ("save_states", C.c_int), ("variant", C.c_int)]
 
 
 class InitSpec(C.Structure):
@@ -122,10 +122,11 @@ class Config:
     precision: int = FP64
     form: int = FUSED
     save_states: int = 0
+    variant: int = 0
 
     def params(self) -> Params:
         return Params(self.alpha_s, self.Nc, self.deriv_type, self.max_jumps, self.r_max, self.l_cap, self.use_rmin,
-                      self.precision, self.form, self.save_states)
+                      self.precision, self.form, self.save_states, self.variant)
 
 
 def init_spec(kind="gauss", width=0.2, n=1, l=0, color=0) -> InitSpec:
