@@ -337,7 +337,12 @@ def run_profile_case(args):
 
     from paper_2107_06147_gb300 import inputs, qtraj
     w = inputs.uniform_interleaved(per_group=10000, N=N_GRID, L=L_BOX, dt=DT)
-    B = max(18, (args.batch // 18) * 18)
+    probe = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=qtraj.FP32 if args.precision == "fp32"
+                                      else qtraj.FP64, variant=args.variant))
+    ki = probe.kernel_info()
+    probe.close()
+    # one full wave of CTAs unless --batch is given explicitly
+    B = args.batch if args.batch_given else ki.sm_count * ki.ctas_per_sm
     tau_end = 0.6 + args.profile_steps * DT * 0.1973269804
     media = [qtraj.medium(m.T0, m.tau0, m.T0 * (m.tau0 / tau_end) ** (1 / 3) * (1 + 1e-9), m.kappa_hat, m.gamma_hat)
              for m in w.media]
@@ -371,6 +376,7 @@ def main():
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
     ap.add_argument("--profile-steps", type=int, default=1000)
     args = ap.parse_args()
+    args.batch_given = any(a.startswith("--batch") for a in sys.argv[1:])
     if args.profile_case:
         from paper_2107_06147_gb300 import build
         build.build()

@@ -61,8 +61,9 @@ typedef struct {
     int precision;   /* qtraj_precision */
     int form;        /* qtraj_form */
     int save_states; /* 1: keep every final u(r) (FP64) in the workspace for qtraj_states()     */
-    int variant;     /* fused kernel occupancy target: 0 = 512 resident threads per SM, 1 = 640
-                        (FP32, N in {2048, 4096}; elsewhere the same as 0)                        */
+    int variant;     /* fused kernel variant (FP32, N in {2048, 4096}; elsewhere the same as 0):
+                        0 = radix 16, 512 resident threads per SM; 1 = radix 16, 640;
+                        2 = radix 8, 768; 3 = radix 8, 1024                                        */
 } qtraj_params;
 
 /* Initial state (Table 1, initType/initWidth/initN/initL/initC): kind 0 is the Gaussian

@@ -270,7 +270,7 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     if (p.precision != QTRAJ_FP64 && p.precision != QTRAJ_FP32) return fail(QTRAJ_EINVAL, "unknown precision");
     if (p.form != QTRAJ_FUSED && p.form != QTRAJ_PLAIN) return fail(QTRAJ_EINVAL, "unknown form");
     if (p.form == QTRAJ_PLAIN && p.precision != QTRAJ_FP64) return fail(QTRAJ_EINVAL, "the plain form is FP64 only");
-    if (p.variant != 0 && p.variant != 1) return fail(QTRAJ_EINVAL, "variant must be 0 or 1");
+    if (p.variant < 0 || p.variant > 3) return fail(QTRAJ_EINVAL, "variant must be in 0..3");
     if (p.form == QTRAJ_FUSED && p.precision == QTRAJ_FP64 && N > 8192)
         return fail(QTRAJ_EINVAL, "the fused FP64 form supports N <= 8192");
 
@@ -447,6 +447,8 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
             const double f = col == 0 ? 0.5 : (Nc * Nc - 2.0) / (4.0 * (Nc * Nc - 1.0));
             md[m].er[col] = -f * q.kappa_hat * c->dt * 0.5;
             md[m].ei[col] = -f * q.gamma_hat * c->dt * 0.5;
+            md[m].erj[col] = md[m].er[col] * c->dr * c->dr;
+            md[m].eij[col] = md[m].ei[col] * c->dr * c->dr / PI;
         }
     }
     std::vector<TrajDev> tr(batch);

@@ -35,13 +35,15 @@
 
 namespace qt {
 
-template <int N> struct FusedPlan {
-    static constexpr int R = (N <= 32) ? 4 : (N <= 512) ? 8 : 16;
+// V selects the launch variant (fused_launch.cuh); variants 2 and 3 use radix 8 for N >= 1024:
+// twice the threads per trajectory, half the registers per thread, one more FFT pass.
+template <int N, int V = 0> struct FusedPlan {
+    static constexpr int R = (N <= 32) ? 4 : (N <= 512) ? 8 : (V >= 2 ? 8 : 16);
     static constexpr int G = N / (2 * R);        // threads per trajectory
     static constexpr int NR = N / R;             // stride of a first/last-pass butterfly
     static constexpr int MID = N / (R * R);      // product of the middle radices
     static constexpr int M1 = MID >= 16 ? 16 : MID;
-    static constexpr int M2 = MID / M1;          // 1, 2 or 4
+    static constexpr int M2 = MID / M1;          // 1, 2, 4, 8 or 16
     static constexpr int BUF = N + N / R + 8;    // padded FFT extent; also holds the E/odd layout
     static_assert(N == R * M1 * M2 * R, "plan");
 };
@@ -174,15 +176,34 @@ template <int G> __device__ __forceinline__ double slot_sum(double v, double *re
     return cross_warp<G>(v, red);
 }
 
+// squared norm over the G threads of a trajectory; FP32 forms reduce in double-float all the way and
+// convert once, so no FP64 instruction is needed per thread beyond the final conversion
 template <typename T, int G> __device__ __forceinline__ double slot_norm(SqAcc<T> acc, double *red)
 {
     constexpr int W = G < 32 ? G : 32;
     const unsigned mask = lane_mask<G>();
 #pragma unroll
     for (int off = W / 2; off > 0; off >>= 1) acc.shfl_add(mask, off, W);
-    double v = acc.value();
-    if constexpr (G <= 32) v = __shfl_sync(mask, v, 0, W);
-    return cross_warp<G>(v, red);
+    if constexpr (sizeof(T) == 4) {
+        DF v = acc.v;
+        if constexpr (G <= 32) {
+            v.hi = __shfl_sync(mask, v.hi, 0, W);
+            v.lo = __shfl_sync(mask, v.lo, 0, W);
+        } else {
+            DF *fr = reinterpret_cast<DF *>(red);
+            if ((threadIdx.x & 31) == 0) fr[threadIdx.x >> 5] = v;
+            __syncthreads();
+            v = fr[0];
+#pragma unroll
+            for (int w = 1; w < G / 32; ++w) v = df_add(v, fr[w]);
+            __syncthreads();
+        }
+        return (double)v.hi + (double)v.lo;
+    } else {
+        double v = acc.value();
+        if constexpr (G <= 32) v = __shfl_sync(mask, v, 0, W);
+        return cross_warp<G>(v, red);
+    }
 }
 
 // exp(x) and (cos, sin)(pi y): the pi-scaled form has no large-argument reduction path
@@ -243,8 +264,8 @@ template <typename T, int RR> struct DFTI {
 // ------------------------------------------------------------------------------------------------
 // the sine transform
 // ------------------------------------------------------------------------------------------------
-template <typename T, int N> struct Fused {
-    using P = FusedPlan<N>;
+template <typename T, int N, int V> struct Fused {
+    using P = FusedPlan<N, V>;
     using PR = Prec<T>;
     using C = typename Prec<T>::C;
     using RL = typename Prec<T>::Rl;
@@ -426,8 +447,8 @@ template <typename T, int N> struct Fused {
 // pointwise work on the E/odd layout: thread g visits k = g, g + G, ... < N/2 and the two elements
 // S_{2k} (at [k]) and S_{2k+1} (at odd_pos(k))
 // ------------------------------------------------------------------------------------------------
-template <typename T, int N> struct Pointwise {
-    using K = Fused<T, N>;
+template <typename T, int N, int V> struct Pointwise {
+    using K = Fused<T, N, V>;
     using PR = Prec<T>;
     using C = typename Prec<T>::C;
     static constexpr int G = K::G;
@@ -442,18 +463,14 @@ template <typename T, int N> struct Pointwise {
     // mode 0: x <- stat1 dyn_b x (the first half-step of a trajectory)
     // mode 1: x <- stat2 dyn_a dyn_b x; returns sum exp(2 er_a r^2) |x_old|^2 (end-of-step norm / dr)
     // mode 2: x <- stat1 dyn_a x; returns sum |x_new|^2
-    // dyn = exp((er + i ei) r^2) with er, ei already multiplied by T^3.  The coefficients enter times
-    // dr^2 and the phase divided by pi, rounded once per call, and multiply the exact j twice: no
+    // dyn = exp((er + i ei) r^2), er and ei multiplied by T^3.  The caller passes the summed
+    // coefficients times dr^2 (phase / pi): A for the magnitude, B for the phase, D = (er_a - er_b) dr^2
+    // for the norm weight; they are rounded once per step and multiply the exact j twice, so no
     // rounding that repeats identically every step enters the arguments.
-    static __device__ double factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode, double er_a,
-                                    double ei_a, double er_b, double ei_b, double *red)
+    static __device__ double factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode, T A, T B, T D,
+                                    double *red)
     {
-        constexpr double INV_PI = 0.31830988618379067154;
         const C *tab = (mode == 1) ? tb.statV2 : tb.statV;
-        const double dr2 = tb.dr * tb.dr;
-        const double ers = (mode == 0 ? 0.0 : er_a) + (mode == 2 ? 0.0 : er_b);
-        const double eis = (mode == 0 ? 0.0 : ei_a) + (mode == 2 ? 0.0 : ei_b);
-        const T A = (T)(ers * dr2), B = (T)(eis * dr2 * INV_PI), D = (T)((er_a - er_b) * dr2);
         SqAcc<T> acc;
 #pragma unroll 2
         for (int k = g; k < N / 2; k += G) {
@@ -577,24 +594,24 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
 }
 
 // Occupancy target of a kernel variant: variant 0 asks for 512 resident threads per SM in FP32
-// (<= 128 registers), variant 1 for 640 (<= 102 registers, at the price of some spills).  FP64
-// holds twice the state and takes what the compiler needs.
+// (<= 128 registers), variant 1 for 640 (<= 102 registers, at the price of some spills), variants 2
+// and 3 (radix 8) for 768 and 1024.  FP64 holds twice the state and takes what the compiler needs.
 template <typename T, int N, int V> struct FusedBounds {
-    static constexpr int G = FusedPlan<N>::G;
-    static constexpr int THREADS = V == 0 ? 512 : 640;
+    static constexpr int G = FusedPlan<N, V>::G;
+    static constexpr int THREADS = V == 0 ? 512 : V == 1 ? 640 : V == 2 ? 768 : 1024;
     static constexpr int MB = THREADS / G > 32 ? 32 : (THREADS / G > 0 ? THREADS / G : 1);
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? MB : 1;
 };
 
 template <typename T, int N, int V>
-__global__ void __launch_bounds__(FusedPlan<N>::G, (FusedBounds<T, N, V>::MIN_BLOCKS)) fused_kernel(Tables<T> tb, LaunchArgs a)
+__global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN_BLOCKS)) fused_kernel(Tables<T> tb, LaunchArgs a)
 {
-    using K = Fused<T, N>;
-    using PW = Pointwise<T, N>;
+    using K = Fused<T, N, V>;
+    using PW = Pointwise<T, N, V>;
     constexpr int G = K::G, E = K::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T> *buf = reinterpret_cast<cpx<T> *>(smem_raw);
-    Carry<T> *wtot = reinterpret_cast<Carry<T> *>(buf + FusedPlan<N>::BUF);
+    Carry<T> *wtot = reinterpret_cast<Carry<T> *>(buf + FusedPlan<N, V>::BUF);
     double *red = reinterpret_cast<double *>(wtot + (G / 32 + 1));
     __shared__ int s_traj;
 
@@ -623,23 +640,26 @@ __global__ void __launch_bounds__(FusedPlan<N>::G, (FusedBounds<T, N, V>::MIN_BL
         double thr = a.nojump ? -1.0 : dw.r;
         int nj = 0, flags = 0, fj = -1, ended = 0, executed = 0;
         const int ns = d.n_steps;
-        double T3b = md.A / md.tau0;
+        // per-step scalars in the working precision: T^3 = A / (tau0 + n dtau)
+        const T mA = (T)md.A, mtau0 = (T)md.tau0, mdtau = (T)md.dtau;
+        T T3b = mA / mtau0;
         if (ns > 0) {
             __syncthreads();
-            PW::factor(buf, tb, g, c, l, 0, 0.0, 0.0, md.er[c] * T3b, md.ei[c] * T3b, red);
+            PW::factor(buf, tb, g, c, l, 0, (T)md.erj[c] * T3b, (T)md.eij[c] * T3b, (T)0, red);
         }
 
         for (int n = 0; n < ns; ++n) {
-            const double T3a = T3b;
+            const T T3a = T3b;
             const bool last = (n + 1 == ns);
-            T3b = md.A / (md.tau0 + (double)(n + 1) * md.dtau);
+            T3b = mA / (mtau0 + (T)(n + 1) * mdtau);
             __syncthreads();
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) K::dst(x, buf, tb, g, wtot, h == 1);
             executed = n + 1;
-            const double er_a = md.er[c] * T3a, ei_a = md.ei[c] * T3a;
-            const double er_b = last ? 0.0 : md.er[c] * T3b, ei_b = last ? 0.0 : md.ei[c] * T3b;
-            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, er_a, ei_a, er_b, ei_b, red) * dr;
+            const T erj = (T)md.erj[c], eij = (T)md.eij[c];
+            const T Tsum = last ? T3a : T3a + T3b;
+            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Tsum, eij * Tsum,
+                                         last ? (T)0 : erj * (T3a - T3b), red) * dr;
             if (!isfinite(n2)) {
                 flags |= QTRAJ_F_NONFINITE;
                 ended = 1;
@@ -666,9 +686,9 @@ __global__ void __launch_bounds__(FusedPlan<N>::G, (FusedBounds<T, N, V>::MIN_BL
                     // r times the end-of-step state, renormalised; the start half-step already applied
                     // is turned into the new colour's and l's
                     __syncthreads();
-                    const double erb = er_b;
-                    const double d_er = last ? 0.0 : (md.er[c_new] - md.er[c]) * T3b;
-                    const double d_ei = last ? 0.0 : (md.ei[c_new] - md.ei[c]) * T3b;
+                    const double erb = last ? 0.0 : md.er[c] * (double)T3b;
+                    const double d_er = last ? 0.0 : (md.er[c_new] - md.er[c]) * (double)T3b;
+                    const double d_ei = last ? 0.0 : (md.ei[c_new] - md.ei[c]) * (double)T3b;
                     const double s = PW::jump_turn(buf, tb, g, c, l, c_new, l_new, last, erb, d_er, d_ei, red) * dr;
                     const double f = 1.0 / sqrt(s);
                     __syncthreads();
@@ -749,10 +769,10 @@ __global__ void __launch_bounds__(FusedPlan<N>::G, (FusedBounds<T, N, V>::MIN_BL
 }
 
 // shared-memory bytes of one CTA
-template <typename T, int N> constexpr int fused_smem_bytes()
+template <typename T, int N, int V> constexpr int fused_smem_bytes()
 {
-    return FusedPlan<N>::BUF * (int)sizeof(cpx<T>) + (FusedPlan<N>::G / 32 + 1) * (int)sizeof(Carry<T>) +
-           (FusedPlan<N>::G / 32 + 1) * 8 + 16;
+    return FusedPlan<N, V>::BUF * (int)sizeof(cpx<T>) + (FusedPlan<N, V>::G / 32 + 1) * (int)sizeof(Carry<T>) +
+           (FusedPlan<N, V>::G / 32 + 1) * 8 + 16;
 }
 
 } // namespace qt

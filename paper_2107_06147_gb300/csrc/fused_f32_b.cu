@@ -11,8 +11,8 @@ cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int m
                bool query_only)
 {
     auto k = fused_kernel<float, N, V>;
-    constexpr int G = FusedPlan<N>::G;
-    constexpr int smem = fused_smem_bytes<float, N>();
+    constexpr int G = FusedPlan<N, V>::G;
+    constexpr int smem = fused_smem_bytes<float, N, V>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -24,7 +24,7 @@ cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int m
         e = cudaFuncGetAttributes(&fa, k);
         if (e != cudaSuccess) return e;
         info->G = G;
-        info->R = FusedPlan<N>::R;
+        info->R = FusedPlan<N, V>::R;
         info->smem = smem;
         info->ctas_per_sm = occ;
         info->regs = fa.numRegs;
@@ -42,10 +42,20 @@ cudaError_t fused_launch_f32_b(int N, const Tables<float> &tb, const LaunchArgs 
                              cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
     switch (N) {
-    case 2048: return variant == 1 ? go<2048, 1>(tb, a, sm_count, max_ctas, s, info, query_only)
-                          : go<2048, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 4096: return variant == 1 ? go<4096, 1>(tb, a, sm_count, max_ctas, s, info, query_only)
-                          : go<4096, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 2048:
+        switch (variant) {
+        case 1: return go<2048, 1>(tb, a, sm_count, max_ctas, s, info, query_only);
+        case 2: return go<2048, 2>(tb, a, sm_count, max_ctas, s, info, query_only);
+        case 3: return go<2048, 3>(tb, a, sm_count, max_ctas, s, info, query_only);
+        default: return go<2048, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+        }
+    case 4096:
+        switch (variant) {
+        case 1: return go<4096, 1>(tb, a, sm_count, max_ctas, s, info, query_only);
+        case 2: return go<4096, 2>(tb, a, sm_count, max_ctas, s, info, query_only);
+        case 3: return go<4096, 3>(tb, a, sm_count, max_ctas, s, info, query_only);
+        default: return go<4096, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+        }
     default: return fused_launch_f32_c(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);
     }
 }

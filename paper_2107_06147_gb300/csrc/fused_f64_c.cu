@@ -9,8 +9,8 @@ cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int 
                bool query_only)
 {
     auto k = fused_kernel<double, N, V>;
-    constexpr int G = FusedPlan<N>::G;
-    constexpr int smem = fused_smem_bytes<double, N>();
+    constexpr int G = FusedPlan<N, V>::G;
+    constexpr int smem = fused_smem_bytes<double, N, V>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -22,7 +22,7 @@ cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int 
         e = cudaFuncGetAttributes(&fa, k);
         if (e != cudaSuccess) return e;
         info->G = G;
-        info->R = FusedPlan<N>::R;
+        info->R = FusedPlan<N, V>::R;
         info->smem = smem;
         info->ctas_per_sm = occ;
         info->regs = fa.numRegs;

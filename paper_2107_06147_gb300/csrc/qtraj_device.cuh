@@ -263,6 +263,8 @@ struct MediumDev {
     double dtau;    // dt * hbar c, fm/c per step
     double er[2];   // -kappa_c dt/2 per colour: the real exponent of the space kernel is er*T^3*r^2
     double ei[2];   // -gamma_c dt/2 per colour: the phase of the space kernel is ei*T^3*r^2
+    double erj[2];  // er * dr^2: the real exponent is erj * T^3 * j^2 on grid point j
+    double eij[2];  // ei * dr^2 / pi: the phase is pi * eij * T^3 * j^2
 };
 
 struct TrajDev {
