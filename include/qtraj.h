@@ -167,6 +167,36 @@ typedef struct {
 } qtraj_kernel_info;
 qtraj_status qtraj_kernel_info_get(const qtraj_ctx *ctx, qtraj_kernel_info *out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Evolving without allocating.  (The paper has no counterpart: its program runs on CPUs only.)
+ *
+ * For callers that cannot allocate at the point of the call -- a service that hands all device
+ * memory to its own pool at start-up and must not touch the CUDA allocator afterwards, or a
+ * latency-bound loop in which an allocation could synchronise the device or fail under
+ * fragmentation.  qtraj_evolve_static runs the fused form (the context's precision and options)
+ * for `batch` trajectories given entirely by host arrays -- initial-state specs with a per-trajectory
+ * index, media with a per-trajectory index (NULL index: as in qtraj_init/qtraj_evolve), seeds -- and
+ * writes batch qtraj_obs records to the device buffer d_out.  It needs no qtraj_init and no
+ * workspace, and it calls no cudaMalloc, cudaFree, cudaMallocHost or any other allocating routine:
+ * every intermediate lives in one fixed device array inside the library (about 2 MB, held by every
+ * device that loads the library until the process exits) and in fixed host arrays.
+ *
+ * Limits: batch <= QTRAJ_STATIC_MAX_TRAJ, n_specs <= QTRAJ_STATIC_MAX_SPECS,
+ * n_media <= QTRAJ_STATIC_MAX_MEDIA, N <= 16384; larger requests return QTRAJ_EINVAL with a message.
+ * The first call on a device looks up the device address of that array (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  All calls share the one array
+ * (the work counter and status word are cleared by every call): calls whose GPU work overlaps -- on
+ * different streams, or from different host threads without ordering -- race on it and must be
+ * serialised by the caller (the host side of the call is serialised by a lock).  Asynchronous on
+ * `stream`; the host arrays may be reused when the call returns.
+ * --------------------------------------------------------------------------------------------- */
+#define QTRAJ_STATIC_MAX_TRAJ 4096
+#define QTRAJ_STATIC_MAX_SPECS 8
+#define QTRAJ_STATIC_MAX_MEDIA 64
+qtraj_status qtraj_evolve_static(qtraj_ctx *ctx, int batch, const qtraj_init_spec *specs, int n_specs,
+                                 const int *spec_idx, const qtraj_medium *media, int n_media, const int *medium_idx,
+                                 const uint64_t *seeds, qtraj_obs *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

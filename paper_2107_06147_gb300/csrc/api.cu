@@ -657,3 +657,238 @@ qtraj_status qtraj_kernel_info_get(const qtraj_ctx *c, qtraj_kernel_info *out)
 }
 
 } // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// qtraj_evolve_static: the fused evolve without any allocation.
+//
+// Some callers cannot call cudaMalloc (or any allocator) at the point where they evolve
+// trajectories: a service that reserves all device memory for a pool at start-up and must not touch
+// the CUDA allocator afterwards, or a latency-bound loop in which an allocation could synchronise the
+// device or fail under fragmentation.  This entry point needs no workspace: everything the fused
+// kernel uses besides its inputs and outputs (trajectory and group descriptors, the no-jump records,
+// the media, the initial states, the work counter and the status word) lives in one file-scope
+// device array of fixed size, and the host-side staging uses file-scope host arrays.  The caller
+// passes host inputs and a device output buffer.
+// ------------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int ST_MAX_TRAJ = QTRAJ_STATIC_MAX_TRAJ;
+constexpr int ST_MAX_SPECS = QTRAJ_STATIC_MAX_SPECS;
+constexpr int ST_MAX_MEDIA = QTRAJ_STATIC_MAX_MEDIA;
+constexpr int ST_MAX_N = 16384;
+
+struct StaticScratch {
+    TrajDev trajs[ST_MAX_TRAJ];
+    TrajDev gtrajs[ST_MAX_TRAJ];
+    qtraj_obs gobs[ST_MAX_TRAJ];
+    MediumDev media[ST_MAX_MEDIA];
+    double ic[ST_MAX_SPECS * ST_MAX_N];
+    double ov0[ST_MAX_SPECS * NBASIS * 2];
+    int ov0_zero[ST_MAX_SPECS * NBASIS];
+    int spec_l[ST_MAX_SPECS];
+    int spec_color[ST_MAX_SPECS];
+    int counter_status[64];   // [0] work counter, [1] status word; cleared by every call
+};
+
+// The device scratch of every call on a device.  Host code must not use this name as an address:
+// on the host it is only a stand-in for the symbol; its device address comes from
+// cudaGetSymbolAddress (st_setup).
+static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScratch)];
+
+// host-side staging, also fixed in size
+StaticScratch g_static_host;
+int g_static_pair_group[ST_MAX_SPECS * ST_MAX_MEDIA];
+std::mutex g_static_mutex;
+constexpr int ST_MAX_DEVICES = 64;
+StaticScratch *g_static_dev[ST_MAX_DEVICES] = {nullptr};
+
+// once per device, with that device current: the device address of the scratch array
+qtraj_status st_setup(int dev, StaticScratch **out)
+{
+    if (dev < 0 || dev >= ST_MAX_DEVICES) return fail(QTRAJ_EINVAL, "device %d beyond the static table", dev);
+    if (!g_static_dev[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(QTRAJ_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        g_static_dev[dev] = (StaticScratch *)p;
+    }
+    *out = g_static_dev[dev];
+    return QTRAJ_OK;
+}
+
+// discretely normalised initial states into a caller-provided array (no allocation)
+void st_coulomb(int N, double dr, double a0, int n, int l, double *u)
+{
+    double s = 0.0;
+    u[0] = 0.0;
+    for (int j = 1; j < N; ++j) {
+        const double r = j * dr;
+        const double v = std::pow(r, l + 1) * std::exp(-r / (n * a0)) * laguerre(n - l - 1, 2 * l + 1, 2.0 * r / (n * a0));
+        u[j] = v;
+        s += v * v;
+    }
+    const double c = 1.0 / std::sqrt(s * dr);
+    for (int j = 1; j < N; ++j) u[j] *= c;
+}
+void st_gauss(int N, double dr, double w, int l, double *u)
+{
+    double s = 0.0;
+    u[0] = 0.0;
+    for (int j = 1; j < N; ++j) {
+        const double r = j * dr;
+        const double v = std::pow(r, l + 1) * std::exp(-r * r / (2.0 * w * w));
+        u[j] = v;
+        s += v * v;
+    }
+    const double c = 1.0 / std::sqrt(s * dr);
+    for (int j = 1; j < N; ++j) u[j] *= c;
+}
+// overlap of a discretely normalised Coulomb state with u, without storing the basis state
+double st_overlap(int N, double dr, double a0, int n, int l, const double *u)
+{
+    double s = 0.0, o = 0.0;
+    for (int j = 1; j < N; ++j) {
+        const double r = j * dr;
+        const double v = std::pow(r, l + 1) * std::exp(-r / (n * a0)) * laguerre(n - l - 1, 2 * l + 1, 2.0 * r / (n * a0));
+        s += v * v;
+        o += v * u[j];
+    }
+    return o / std::sqrt(s * dr) * dr;
+}
+
+} // namespace
+
+extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj_init_spec *specs, int n_specs,
+                                            const int *spec_idx, const qtraj_medium *media, int n_media,
+                                            const int *medium_idx, const uint64_t *seeds, qtraj_obs *d_out,
+                                            void *stream)
+{
+    g_err.clear();
+    if (!c || !specs || !media || !seeds || !d_out) return fail(QTRAJ_EINVAL, "null argument");
+    if (c->p.form != QTRAJ_FUSED) return fail(QTRAJ_EINVAL, "qtraj_evolve_static runs the fused form only");
+    if (batch < 0 || batch > ST_MAX_TRAJ)
+        return fail(QTRAJ_EINVAL, "batch %d outside [0, %d] (QTRAJ_STATIC_MAX_TRAJ)", batch, ST_MAX_TRAJ);
+    if (n_specs <= 0 || n_specs > ST_MAX_SPECS)
+        return fail(QTRAJ_EINVAL, "n_specs %d outside [1, %d] (QTRAJ_STATIC_MAX_SPECS)", n_specs, ST_MAX_SPECS);
+    if (n_media <= 0 || n_media > ST_MAX_MEDIA)
+        return fail(QTRAJ_EINVAL, "n_media %d outside [1, %d] (QTRAJ_STATIC_MAX_MEDIA)", n_media, ST_MAX_MEDIA);
+    if (c->N > ST_MAX_N) return fail(QTRAJ_EINVAL, "N %d above %d", c->N, ST_MAX_N);
+    if (!spec_idx && n_specs != 1 && n_specs != batch)
+        return fail(QTRAJ_EINVAL, "spec_idx is required unless n_specs is 1 or batch");
+    if (!medium_idx && n_media != 1 && n_media != batch)
+        return fail(QTRAJ_EINVAL, "medium_idx is required unless n_media is 1 or batch");
+    if (((uintptr_t)d_out & 7) != 0) return fail(QTRAJ_EINVAL, "d_out must be 8-byte aligned");
+
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(QTRAJ_ECUDA, "cudaGetDevice failed");
+    StaticScratch *ds = nullptr;
+    const qtraj_status sst = st_setup(dev, &ds);
+    if (sst != QTRAJ_OK) return sst;
+
+    const int N = c->N;
+    StaticScratch &h = g_static_host;
+    for (int s = 0; s < n_specs; ++s) {
+        const qtraj_init_spec &q = specs[s];
+        if (q.kind != 0 && q.kind != 1) return fail(QTRAJ_EINVAL, "spec %d: kind must be 0 or 1", s);
+        if (q.l < 0 || (q.color != 0 && q.color != 1)) return fail(QTRAJ_EINVAL, "spec %d: l >= 0, color 0/1", s);
+        if (q.kind == 0 && !(q.width > 0)) return fail(QTRAJ_EINVAL, "spec %d: width must be positive", s);
+        if (q.kind == 1 && (q.n < 1 || q.l >= q.n)) return fail(QTRAJ_EINVAL, "spec %d: need 0 <= l < n", s);
+        double *u = h.ic + (size_t)s * N;
+        if (q.kind == 1) st_coulomb(N, c->dr, c->a0, q.n, q.l, u);
+        else st_gauss(N, c->dr, q.width, q.l, u);
+        h.spec_l[s] = q.l;
+        h.spec_color[s] = q.color;
+        for (int b = 0; b < NBASIS; ++b) {
+            const int z = q.color != 0 || q.l != BASIS_L[b] || (q.kind == 1 && q.n != BASIS_N[b]);
+            h.ov0_zero[s * NBASIS + b] = z;
+            h.ov0[(s * NBASIS + b) * 2] = z ? 0.0 : st_overlap(N, c->dr, c->a0, BASIS_N[b], BASIS_L[b], u);
+            h.ov0[(s * NBASIS + b) * 2 + 1] = 0.0;
+        }
+    }
+    const double Nc = c->p.Nc;
+    int steps[ST_MAX_MEDIA];
+    for (int m = 0; m < n_media; ++m) {
+        const qtraj_medium &q = media[m];
+        if (q.kind != 0) return fail(QTRAJ_EINVAL, "medium %d: only kind 0 (Bjorken) is supported", m);
+        if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return fail(QTRAJ_EINVAL, "medium %d: T0, tau0, Tf > 0", m);
+        if (!(q.kappa_hat >= 0) || !(q.gamma_hat <= 0))
+            return fail(QTRAJ_EINVAL, "medium %d: kappa_hat >= 0 and gamma_hat <= 0 required", m);
+        steps[m] = medium_steps(c->dt, q);
+        MediumDev &d = h.media[m];
+        d.A = q.T0 * q.T0 * q.T0 * q.tau0;
+        d.tau0 = q.tau0;
+        d.dtau = c->dt * HBARC;
+        for (int col = 0; col < 2; ++col) {
+            const double f = col == 0 ? 0.5 : (Nc * Nc - 2.0) / (4.0 * (Nc * Nc - 1.0));
+            d.er[col] = -f * q.kappa_hat * c->dt * 0.5;
+            d.ei[col] = -f * q.gamma_hat * c->dt * 0.5;
+            d.erj[col] = d.er[col] * c->dr * c->dr;
+            d.eij[col] = d.ei[col] * c->dr * c->dr / PI;
+        }
+    }
+    for (int i = 0; i < n_specs * n_media; ++i) g_static_pair_group[i] = -1;
+    int n_groups = 0;
+    for (int t = 0; t < batch; ++t) {
+        const int sp = spec_idx ? spec_idx[t] : (n_specs == 1 ? 0 : t);
+        const int mi = medium_idx ? medium_idx[t] : (n_media == 1 ? 0 : t);
+        if (sp < 0 || sp >= n_specs) return fail(QTRAJ_EINVAL, "spec_idx[%d] out of range", t);
+        if (mi < 0 || mi >= n_media) return fail(QTRAJ_EINVAL, "medium_idx[%d] out of range", t);
+        int &gidx = g_static_pair_group[sp * n_media + mi];
+        if (gidx < 0) {
+            gidx = n_groups;
+            h.gtrajs[n_groups] = TrajDev{0ull, sp, mi, steps[mi], n_groups};
+            ++n_groups;
+        }
+        h.trajs[t] = TrajDev{(unsigned long long)seeds[t], sp, mi, steps[mi], gidx};
+    }
+    if (!c->p.use_rmin) n_groups = 0;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    auto up = [&](void *dst, const void *src, size_t n) -> cudaError_t {
+        return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    CK(up(ds->ic, h.ic, sizeof(double) * (size_t)n_specs * N));
+    CK(up(ds->ov0, h.ov0, sizeof(double) * n_specs * NBASIS * 2));
+    CK(up(ds->ov0_zero, h.ov0_zero, sizeof(int) * n_specs * NBASIS));
+    CK(up(ds->spec_l, h.spec_l, sizeof(int) * n_specs));
+    CK(up(ds->spec_color, h.spec_color, sizeof(int) * n_specs));
+    CK(up(ds->media, h.media, sizeof(MediumDev) * n_media));
+    CK(up(ds->trajs, h.trajs, sizeof(TrajDev) * batch));
+    CK(up(ds->gtrajs, h.gtrajs, sizeof(TrajDev) * (n_groups > 0 ? n_groups : 0)));
+    // the work counter and the status word must start at zero in every call
+    CK(cudaMemsetAsync(ds->counter_status, 0, sizeof(ds->counter_status), s));
+
+    int *d_ctr = ds->counter_status, *d_status = ds->counter_status + 1;
+    LaunchArgs ga{ds->gtrajs, n_groups, ds->gobs, nullptr, d_ctr, d_status, nullptr, 1};
+    LaunchArgs ma{ds->trajs, batch, d_out, ds->gobs, d_ctr, d_status, nullptr, 0};
+    FusedInfo fi;
+    auto point = [&](auto tb) {
+        tb.ic = ds->ic;
+        tb.ov0 = ds->ov0;
+        tb.ov0_zero = ds->ov0_zero;
+        tb.spec_l = ds->spec_l;
+        tb.spec_color = ds->spec_color;
+        tb.media = ds->media;
+        return tb;
+    };
+    if (c->p.precision == QTRAJ_FP32) {
+        const Tables<float> tb = point(tables<float>(c));
+        if (n_groups > 0) {
+            CK(fused_launch_f32(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
+            CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
+        }
+        CK(fused_launch_f32(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
+    } else {
+        const Tables<double> tb = point(tables<double>(c));
+        if (n_groups > 0) {
+            CK(fused_launch_f64(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
+            CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
+        }
+        CK(fused_launch_f64(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
+    }
+    return QTRAJ_OK;
+}

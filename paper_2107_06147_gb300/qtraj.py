@@ -74,6 +74,9 @@ _PROTOS = {
     "qtraj_nojump_results": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "qtraj_last_run_stats": (C.c_int, [C.c_void_p, C.POINTER(RunStats)]),
     "qtraj_kernel_info_get": (C.c_int, [C.c_void_p, C.POINTER(KernelInfo)]),
+    "qtraj_evolve_static": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(InitSpec), C.c_int, C.POINTER(C.c_int),
+                                      C.POINTER(Medium), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint64),
+                                      C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
