@@ -247,12 +247,41 @@ def run_ours(args):
         result["speedup_vs_plain_fp64"] = round(value / world / result["plain_fp64"]["value"], 2)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0 and not args.no_serving:
+        eng.close()
+        result["serving"] = run_serving(args)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    eng.close()
+    if eng.ctx:
+        eng.close()
     if rank == 0:
         print(json.dumps(result))
+
+
+def run_serving(args):
+    """p50/p99 request latency of the continuous-batching loop on the first --serving-requests of the
+    Poisson request stream (200 req/s, seed 1; initial state in {1S, 2S, 1P}, kappa ~ U[3,7],
+    gamma ~ U[-3.5,0], T0 ~ U[0.3,0.6] GeV Bjorken to 0.25 GeV, ntraj log-uniform in [64, 4096],
+    N in {1024, ..., 16384} with L = N * 5/512, dt = 0.001).  The offered rate far exceeds one GPU's
+    service rate, so latency includes queueing behind the earlier requests."""
+    import torch
+
+    from paper_2107_06147_gb300 import inputs, serving
+    st = inputs.serving_stream(n_requests=args.serving_requests, rate_hz=200.0, seed=1)
+    reqs = serving.requests_from_stream(st)
+    Ns = sorted(set(int(n) for n in st["N"]))
+    srv = serving.Server(Ns=tuple(Ns), slots_per_n=2)
+    torch.cuda.synchronize()
+    wall = srv.run_stream(reqs, st["arrival_s"])
+    srv.close()
+    lat = serving.latency_stats(reqs)
+    steps = int(sum(int(r.obs["n_steps_exec"].sum()) for r in reqs))
+    return {"requests": len(reqs), "offered_rate_hz": 200.0, "latency_p50_s": round(lat["p50_s"], 3),
+            "latency_p99_s": round(lat["p99_s"], 3), "latency_mean_s": round(lat["mean_s"], 3),
+            "wall_s": round(wall, 3), "traj_steps": steps, "traj_steps_per_s": round(steps / wall, 1),
+            "completed_rate_hz": round(len(reqs) / wall, 3), "Ns": Ns,
+            "trajectories": int(sum(r.ntraj for r in reqs)), "precision": "fp32 fused, rMin shortcut off"}
 
 
 def measure_form(qtraj, w, specs, media, prec, form, B):
@@ -372,6 +401,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="fused kernel occupancy variant (0 or 1)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
     ap.add_argument("--profile-steps", type=int, default=1000)

@@ -128,6 +128,12 @@ size_t qtraj_workspace_bytes(const qtraj_ctx *ctx, int n_traj);
 qtraj_status qtraj_init(qtraj_ctx *ctx, void *d_workspace, size_t bytes, int n_traj,
                         const qtraj_init_spec *specs, int n_specs, const int *spec_idx);
 
+/* Re-binds the initial state of trajectories [0, n) to specs[spec_idx[t]] of the last qtraj_init,
+ * without touching the device (host bookkeeping only; takes effect at the next qtraj_evolve).  Lets a
+ * scheduler reuse one bound workspace for batches of different composition.  EINVAL if n exceeds the
+ * bound n_traj or an index is out of range. */
+qtraj_status qtraj_set_spec_idx(qtraj_ctx *ctx, const int *spec_idx, int n);
+
 /* Evolves trajectories [0, batch) of the bound workspace through their media: trajectory t sees
  * media[medium_idx[t]] (same NULL rule as qtraj_init) and draws its waiting-time thresholds and
  * jump choices from Philox4x32-10 keyed by seeds[t] (host array of batch entries).  With use_rmin,

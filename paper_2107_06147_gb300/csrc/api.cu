@@ -417,6 +417,18 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
     return QTRAJ_OK;
 }
 
+qtraj_status qtraj_set_spec_idx(qtraj_ctx *c, const int *spec_idx, int n)
+{
+    g_err.clear();
+    if (!c || !spec_idx) return fail(QTRAJ_EINVAL, "null argument");
+    if (!c->ws) return fail(QTRAJ_EINVAL, "qtraj_init has not bound a workspace");
+    if (n <= 0 || n > c->n_traj) return fail(QTRAJ_EINVAL, "n %d outside [1, %d]", n, c->n_traj);
+    for (int t = 0; t < n; ++t)
+        if (spec_idx[t] < 0 || spec_idx[t] >= c->n_spec) return fail(QTRAJ_EINVAL, "spec_idx[%d] out of range", t);
+    for (int t = 0; t < n; ++t) c->spec_idx[t] = spec_idx[t];
+    return QTRAJ_OK;
+}
+
 qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, int n_media, const int *medium_idx,
                           const uint64_t *seeds, void *stream)
 {

@@ -67,6 +67,7 @@ _PROTOS = {
     "qtraj_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int]),
     "qtraj_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.POINTER(InitSpec), C.c_int,
                              C.POINTER(C.c_int)]),
+    "qtraj_set_spec_idx": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int]),
     "qtraj_evolve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Medium), C.c_int, C.POINTER(C.c_int),
                                C.POINTER(C.c_uint64), C.c_void_p]),
     "qtraj_observables": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -185,6 +186,12 @@ class Engine:
             idx = self._spec_idx.ctypes.data_as(C.POINTER(C.c_int))
         _check(self.lib.qtraj_init(self.ctx, C.c_void_p(ptr), nb, n_traj, arr, len(specs), idx), self.ctx)
         self.n_traj = n_traj
+
+    def set_spec_idx(self, spec_idx):
+        """Re-binds the initial state of trajectories [0, len(spec_idx)) (host-side, no device sync)."""
+        self._spec_idx2 = np.ascontiguousarray(spec_idx, dtype=np.int32)
+        _check(self.lib.qtraj_set_spec_idx(self.ctx, self._spec_idx2.ctypes.data_as(C.POINTER(C.c_int)),
+                                           len(self._spec_idx2)), self.ctx)
 
     def evolve(self, media, seeds, medium_idx=None, batch: int | None = None, stream=None):
         batch = len(seeds) if batch is None else batch
