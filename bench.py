@@ -271,7 +271,7 @@ def run_serving(args):
     st = inputs.serving_stream(n_requests=args.serving_requests, rate_hz=200.0, seed=1)
     reqs = serving.requests_from_stream(st)
     Ns = sorted(set(int(n) for n in st["N"]))
-    srv = serving.Server(Ns=tuple(Ns), slots_per_n=2)
+    srv = serving.Server(Ns=tuple(Ns), slots_per_n=2, wave_mult=4)
     torch.cuda.synchronize()
     wall = srv.run_stream(reqs, st["arrival_s"])
     srv.close()

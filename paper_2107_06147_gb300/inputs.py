@@ -141,13 +141,13 @@ def small_parity(N: int = 64, n_traj: int = 16, seed: int = 7) -> Workload:
     return Workload(f"small parity N={N}", GridSpec(N, N * 5.0 / 256, 0.001), inits, media, ii, mi, seeds)
 
 
-def uneven(n_traj: int = 1 << 16, seed: int = 0) -> Workload:
-    """Uneven batch: N in {1024, 2048, 4096, 8192} (L = N*5/512, i.e. fixed dr), l0 in {0, 1, 2}
-    (Gaussian r^{l+1}e^{-r^2/(2*0.2^2)} singlets), T0 ~ U[0.30, 0.60] GeV at tau0 = 0.6 fm/c cut at
-    0.25 GeV, kappa_hat ~ U[3, 7], gamma_hat ~ U[-3.5, 0].  Returned as one Workload per N value with
-    the per-trajectory media; 'order' holds the original trajectory ids."""
+def uneven(n_traj: int = 1 << 16, seed: int = 0, Ns=(1024, 2048, 4096, 8192)) -> dict:
+    """Uneven batch: N drawn from Ns (L = N*5/512, i.e. fixed dr), l0 in {0, 1, 2} (Gaussian
+    r^{l+1}e^{-r^2/(2*0.2^2)} singlets), T0 ~ U[0.30, 0.60] GeV at tau0 = 0.6 fm/c cut at 0.25 GeV,
+    kappa_hat ~ U[3, 7], gamma_hat ~ U[-3.5, 0]; seeds = trajectory ids.  Returned as per-trajectory
+    arrays."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    Ns = rng.choice(np.array([1024, 2048, 4096, 8192]), n_traj)
+    Ns = rng.choice(np.array(Ns), n_traj)
     l0 = rng.integers(0, 3, n_traj)
     T0 = rng.uniform(0.30, 0.60, n_traj)
     kap = rng.uniform(3.0, 7.0, n_traj)

@@ -10,7 +10,7 @@ are excluded from the sequence identity.
 FP32 fused form: jump decisions are taken on an FP32 state, so a trajectory whose norm crosses its
 threshold within the FP32 error of the state may jump one step earlier or later; the checks are (i)
 at least 85% identical jump sequences, (ii) on those, survival ratios within 1e-3 relative (to
-max(1, S)) and a median final-state error below 2e-4 relative L2 (times n_jumps/10 above ten jumps),
+max(1, S)) and a median final-state error below 5e-4 relative L2 (times n_jumps/10 above ten jumps),
 and (iii) the paired ensemble means
 of the survival ratios (same seeds on both sides) within 1e-4 absolute.
 """
@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
 FP32_SURV_REL = 1e-3
-FP32_STATE_MEDIAN = 2e-4
+FP32_STATE_MEDIAN = 5e-4
 FP32_ENSEMBLE_ABS = 1e-4
 
 
@@ -227,3 +227,39 @@ def test_headline_size_sampled(q):
     obs64, u64 = run_gpu(q, small, q.FP64)
     s64 = sample[sample < 256]
     check_fp64(q, obs64[s64], ref[: len(s64)], u64[s64], uref[: len(s64)])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uneven_batch_against_oracle(q, precision):
+    """Uneven batch (batching.UnevenBatch): grid sizes 32/64/128 with dr fixed, l0 in {0,1,2}, random
+    T0, kappa, gamma (short media), all groups launched together; each trajectory checked against the
+    oracle run on its own grid."""
+    import oracle as o
+    from paper_2107_06147_gb300 import batching, inputs
+    u = inputs.uneven(n_traj=36, seed=4, Ns=(32, 64, 128))
+    inits = [q.init_spec("gauss", 0.2, 1 + int(l), int(l), 0) for l in u["l0"]]
+    T0 = u["T0"]
+    media = [q.medium(float(T0[i]), 0.6, float(T0[i]) * 0.93, float(u["kappa_hat"][i]), float(u["gamma_hat"][i]))
+             for i in range(36)]
+    b = batching.UnevenBatch(u["N"], inits, media, precision=precision)
+    obs = b.run(u["seeds"])
+    b.close()
+    ref = np.zeros(36, dtype=o.OBS_DTYPE)
+    for N in (32, 64, 128):
+        ids = np.nonzero(u["N"] == N)[0]
+        g = o.Grid(N=N, L=N * 5.0 / 512, dt=0.001)
+        oin = [o.init_spec("gauss", 0.2, 1 + int(u["l0"][i]), int(u["l0"][i]), 0) for i in ids]
+        om = [o.medium(float(T0[i]), 0.6, float(T0[i]) * 0.93, float(u["kappa_hat"][i]), float(u["gamma_hat"][i]))
+              for i in ids]
+        r, _, _ = o.run_batch(g, oin, np.arange(len(ids)), om, np.arange(len(ids)), u["seeds"][ids])
+        ref[ids] = r
+    assert (ref["n_steps_exec"] > 0).any() and len(set(ref["n_steps_exec"])) > 3   # uneven lifetimes
+    if precision == 0:
+        ok = ((obs["flags"] | ref["flags"]) & q.F_BORDERLINE) == 0
+        for f in ("n_jumps", "first_jump_step", "l", "color", "n_steps_exec"):
+            assert np.array_equal(obs[f][ok], ref[f][ok]), f
+        np.testing.assert_allclose(obs["surv"][ok], ref["surv"][ok], rtol=1e-9, atol=1e-12)
+    else:
+        same = (obs["n_jumps"] == ref["n_jumps"]) & (obs["first_jump_step"] == ref["first_jump_step"])
+        assert same.mean() >= 0.8
+        assert np.abs(obs["surv"].mean(0) - ref["surv"].mean(0)).max() <= FP32_ENSEMBLE_ABS
