@@ -370,25 +370,32 @@ template <typename T, int N, int V> struct Fused {
         }
     }
 
+    // One middle pass (radix RM after PP points): butterfly i reads [i + m N/RM], multiplies by
+    // W_{PP RM}^{m k} (k = i mod PP) and writes [(i - k) RM + k + m PP].  A thread's butterflies are
+    // g + q G; when PP <= G they share k = g mod PP and so their twiddles, which are loaded once per m
+    // (from tw, a table of W_{PP RM}^t, t < PP RM).
     template <int RM, int PP>
-    static __device__ __forceinline__ void mid_pass(cpx<T> *x, cpx<T> *buf, const C *W, int g)
+    static __device__ __forceinline__ void mid_pass(cpx<T> *x, cpx<T> *buf, const C *tw, int g)
     {
         if constexpr (RM > 1) {
             constexpr int NB = N / RM, PER = E / RM;
+            static_assert(PP <= G, "mid-pass twiddle sharing needs PP <= G");
+            const int k = g & (PP - 1);
 #pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int i = g + q * G, k = i & (PP - 1);
+            for (int m = 0; m < RM; ++m) {
+                C w{};
+                if (m) w = tw_load(tw, m * k);
 #pragma unroll
-                for (int m = 0; m < RM; ++m) {
-                    cpx<T> v = buf[pad(i + m * NB)];
-                    if (m) v = PR::mul(v, PR::ld(&W[m * k * (N / (PP * RM))]));
+                for (int q = 0; q < PER; ++q) {
+                    cpx<T> v = buf[pad(g + q * G + m * NB)];
+                    if (m) v = PR::mul(v, w);
                     x[q * RM + m] = v;
                 }
             }
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                const int i = g + q * G, k = i & (PP - 1);
+                const int i = g + q * G;
                 DFTI<T, RM>::run(x + q * RM);
                 const int base = (i - k) * RM + k;
 #pragma unroll
@@ -398,9 +405,12 @@ template <typename T, int N, int V> struct Fused {
         }
     }
 
+    // twiddle tables of the middle passes live in shared memory (tw1: W_{R M1}, tw2: W_{R M1 M2})
+    static __device__ __forceinline__ C tw_load(const C *tw, int t) { return tw[t]; }
+
     // S (E/odd layout in buf), optionally times K_T, at the first-pass indices -> DST -> E/odd layout
     static __device__ __forceinline__ void dst(cpx<T> *x, cpx<T> *buf, const Tables<T> &tb, int g, Carry<T> *wtot,
-                                               bool kinetic)
+                                               const C *tw1, const C *tw2, bool kinetic)
     {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -420,18 +430,26 @@ template <typename T, int N, int V> struct Fused {
             for (int k = 0; k < R; ++k) buf[pad(b * R + k)] = x[t * R + DR::operm(k)];
         }
         __syncthreads();
-        mid_pass<P::M1, R>(x, buf, tb.W, g);
-        mid_pass<P::M2, R * P::M1>(x, buf, tb.W, g);
-        // last pass (radix R, stride N/R): inputs [b + m NR], twiddle W^(m b)
+        mid_pass<P::M1, R>(x, buf, tw1, g);
+        mid_pass<P::M2, R * P::M1>(x, buf, tw2, g);
+        // last pass (radix R, stride N/R): inputs [b + m NR], twiddle W^(m b).  For the mirror butterfly
+        // b2 = NR - g, W^(m b2) = W_R^m conj(W^(m g)): one table load serves both (g = 0 pairs
+        // 0 with NR/2, whose twiddles are loaded directly).
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int b = b_of(g, t);
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-                cpx<T> v = buf[pad(b + m * NR)];
-                if (m) v = PR::mul(v, PR::ld(&tb.W[m * b]));
-                x[t * R + m] = v;
+        for (int m = 0; m < R; ++m) {
+            cpx<T> v1 = buf[pad(b_of(g, 0) + m * NR)];
+            cpx<T> v2 = buf[pad(b_of(g, 1) + m * NR)];
+            if (m) {
+                const C w = PR::ld(&tb.W[m * g]);
+                v1 = PR::mul(v1, w);
+                if (g != 0) {
+                    v2 = tw16(PR::mul(v2, PR::conj(w)), m * (16 / R));
+                } else {
+                    v2 = PR::mul(v2, PR::ld(&tb.W[m * (NR / 2)]));
+                }
             }
+            x[m] = v1;
+            x[R + m] = v2;
         }
         __syncthreads();
 #pragma unroll
@@ -507,45 +525,44 @@ template <typename T, int N, int V> struct Pointwise {
     // Returns sum r^2 |end-of-step state|^2 (/ dr); with mode 1 the end-of-step state is
     // exp(-er_b r^2) times the stored one.  With mode 1 it also turns the start half-step already
     // applied from (c, l) into (c2, l2): x <- conj(stat1(c,l)) stat1(c2,l2) exp(d_er r^2 + i d_ei r^2) x.
+    // The coefficients come times dr^2 (the phase also / pi) and multiply j^2: w2 = -2 er_b dr^2,
+    // A = d_er dr^2, B = d_ei dr^2 / pi.  A one-off factor, so working precision suffices.
     static __device__ double jump_turn(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int c2, int l2,
-                                       bool after_last, double er_b, double d_er, double d_ei, double *red)
+                                       bool after_last, T w2, T A, T B, double *red)
     {
-        double s = 0.0;
+        const T dr2 = (T)(tb.dr * tb.dr);
+        SqAcc<T> acc;
         for (int k = g; k < N / 2; k += G) {
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
                 const int p = par ? K::odd_pos(k) : k;
-                const double r = j * tb.dr, r2 = r * r;
-                const cpx<T> v = buf[p];
-                const double a2 = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                const T fj = (T)j, j2 = fj * fj;
+                cpx<T> v = buf[p];
                 if (after_last) {
-                    s += r2 * a2;
+                    acc.add_w(v, dr2 * j2);
                 } else {
-                    s += r2 * exp(-2.0 * er_b * r2) * a2;
-                    const cpx<double> a = to_d(stat(tb, tb.statV, c, l, j, false));
-                    const cpx<double> b = to_d(stat(tb, tb.statV, c2, l2, j, false));
-                    double sn, cs;
-                    sincos(d_ei * r2, &sn, &cs);
-                    const double m = exp(d_er * r2);
-                    const cpx<double> f = mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x) * mk(m * cs, m * sn);
-                    const cpx<double> vd = mk((double)v.x, (double)v.y) * f;
-                    buf[p] = mk<T>((T)vd.x, (T)vd.y);
+                    acc.add_w(v, dr2 * j2 * k_exp(w2 * j2));
+                    v = PR::mul(PR::mul(v, PR::conj(stat(tb, tb.statV, c, l, j, false))), stat(tb, tb.statV, c2, l2, j, false));
+                    T sn, cs;
+                    k_sincospi(B * j2, &sn, &cs);
+                    const T m = k_exp(A * j2);
+                    v = v * mk(m * cs, m * sn);
+                    buf[p] = v;
                 }
             }
         }
-        return slot_sum<G>(s, red);
+        return slot_norm<T, G>(acc, red);
     }
 
     // x <- x * r_j * f
     static __device__ void scale_r(cpx<T> *buf, const Tables<T> &tb, int g, double f)
     {
+        const T s = (T)(tb.dr * f);
         for (int k = g; k < N / 2; k += G) {
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
                 const int p = par ? K::odd_pos(k) : k;
-                const double m = j * tb.dr * f;
-                const cpx<T> v = buf[p];
-                buf[p] = mk<T>((T)((double)v.x * m), (T)((double)v.y * m));
+                buf[p] = scale(buf[p], (T)j * s);
             }
         }
     }
@@ -611,9 +628,16 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
     constexpr int G = K::G, E = K::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T> *buf = reinterpret_cast<cpx<T> *>(smem_raw);
-    Carry<T> *wtot = reinterpret_cast<Carry<T> *>(buf + FusedPlan<N, V>::BUF);
+    using C = typename Prec<T>::C;
+    using P = FusedPlan<N, V>;
+    C *tw1 = reinterpret_cast<C *>(buf + P::BUF);
+    C *tw2 = tw1 + P::R * P::M1;
+    Carry<T> *wtot = reinterpret_cast<Carry<T> *>(tw2 + P::R * P::M1 * P::M2);
     double *red = reinterpret_cast<double *>(wtot + (G / 32 + 1));
     __shared__ int s_traj;
+    // middle-pass twiddles W_{R M1}^t and W_{R M1 M2}^t, copied once per CTA
+    for (int t = threadIdx.x; t < P::R * P::M1; t += G) tw1[t] = Prec<T>::ld(&tb.W[t * (N / (P::R * P::M1))]);
+    for (int t = threadIdx.x; t < P::R * P::M1 * P::M2; t += G) tw2[t] = Prec<T>::ld(&tb.W[t * (N / (P::R * P::M1 * P::M2))]);
 
     const int g = threadIdx.x;
     const double dr = tb.dr;
@@ -654,7 +678,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             T3b = mA / (mtau0 + (T)(n + 1) * mdtau);
             __syncthreads();
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) K::dst(x, buf, tb, g, wtot, h == 1);
+            for (int h = 0; h < 2; ++h) K::dst(x, buf, tb, g, wtot, tw1, tw2, h == 1);
             executed = n + 1;
             const T erj = (T)md.erj[c], eij = (T)md.eij[c];
             const T Tsum = last ? T3a : T3a + T3b;
@@ -686,10 +710,11 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                     // r times the end-of-step state, renormalised; the start half-step already applied
                     // is turned into the new colour's and l's
                     __syncthreads();
-                    const double erb = last ? 0.0 : md.er[c] * (double)T3b;
-                    const double d_er = last ? 0.0 : (md.er[c_new] - md.er[c]) * (double)T3b;
-                    const double d_ei = last ? 0.0 : (md.ei[c_new] - md.ei[c]) * (double)T3b;
-                    const double s = PW::jump_turn(buf, tb, g, c, l, c_new, l_new, last, erb, d_er, d_ei, red) * dr;
+                    const double dr2 = tb.dr * tb.dr, T3d = (double)T3b;
+                    const T w2 = last ? (T)0 : (T)(-2.0 * md.er[c] * T3d * dr2);
+                    const T dA = last ? (T)0 : (T)((md.er[c_new] - md.er[c]) * T3d * dr2);
+                    const T dB = last ? (T)0 : (T)((md.ei[c_new] - md.ei[c]) * T3d * dr2 * 0.31830988618379067154);
+                    const double s = PW::jump_turn(buf, tb, g, c, l, c_new, l_new, last, w2, dA, dB, red) * dr;
                     const double f = 1.0 / sqrt(s);
                     __syncthreads();
                     PW::scale_r(buf, tb, g, f);
@@ -771,8 +796,9 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
 // shared-memory bytes of one CTA
 template <typename T, int N, int V> constexpr int fused_smem_bytes()
 {
-    return FusedPlan<N, V>::BUF * (int)sizeof(cpx<T>) + (FusedPlan<N, V>::G / 32 + 1) * (int)sizeof(Carry<T>) +
-           (FusedPlan<N, V>::G / 32 + 1) * 8 + 16;
+    using P = FusedPlan<N, V>;
+    return P::BUF * (int)sizeof(cpx<T>) + (P::R * P::M1 + P::R * P::M1 * P::M2) * (int)sizeof(typename Prec<T>::C) +
+           (P::G / 32 + 1) * (int)sizeof(Carry<T>) + (P::G / 32 + 1) * 8 + 16;
 }
 
 } // namespace qt

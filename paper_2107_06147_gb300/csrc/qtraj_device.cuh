@@ -52,6 +52,7 @@ template <> struct Prec<double> {
     static __host__ C make(double re, double im) { return {re, im}; }
     static __host__ Rl make_r(double v) { return v; }
     static __device__ __forceinline__ cpx<double> mul(cpx<double> x, C w) { return x * w; }
+    static __device__ __forceinline__ C conj(C w) { return {w.x, -w.y}; }
     static __device__ __forceinline__ cpx<double> mulr(cpx<double> x, Rl s) { return scale(x, s); }
     static __device__ __forceinline__ C ld(const C *p) { return ldg(p); }
     static __device__ __forceinline__ Rl ldr(const Rl *p) { return __ldg(p); }
@@ -75,6 +76,7 @@ template <> struct Prec<float> {
         const float lr = fmaf(x.x, w.rl, -x.y * w.il), li = fmaf(x.x, w.il, x.y * w.rl);
         return {fmaf(x.x, w.rh, fmaf(-x.y, w.ih, lr)), fmaf(x.x, w.ih, fmaf(x.y, w.rh, li))};
     }
+    static __device__ __forceinline__ C conj(C w) { return {w.rh, -w.ih, w.rl, -w.il}; }
     static __device__ __forceinline__ cpx<float> mulr(cpx<float> x, Rl s)
     {
         return {fmaf(x.x, s.h, x.x * s.l), fmaf(x.y, s.h, x.y * s.l)};

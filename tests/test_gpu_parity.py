@@ -239,7 +239,7 @@ def test_uneven_batch_against_oracle(q, precision):
     u = inputs.uneven(n_traj=36, seed=4, Ns=(32, 64, 128))
     inits = [q.init_spec("gauss", 0.2, 1 + int(l), int(l), 0) for l in u["l0"]]
     T0 = u["T0"]
-    media = [q.medium(float(T0[i]), 0.6, float(T0[i]) * 0.93, float(u["kappa_hat"][i]), float(u["gamma_hat"][i]))
+    media = [q.medium(float(T0[i]), 0.6, float(T0[i]) - 0.02, float(u["kappa_hat"][i]), float(u["gamma_hat"][i]))
              for i in range(36)]
     b = batching.UnevenBatch(u["N"], inits, media, precision=precision)
     obs = b.run(u["seeds"])
@@ -249,7 +249,7 @@ def test_uneven_batch_against_oracle(q, precision):
         ids = np.nonzero(u["N"] == N)[0]
         g = o.Grid(N=N, L=N * 5.0 / 512, dt=0.001)
         oin = [o.init_spec("gauss", 0.2, 1 + int(u["l0"][i]), int(u["l0"][i]), 0) for i in ids]
-        om = [o.medium(float(T0[i]), 0.6, float(T0[i]) * 0.93, float(u["kappa_hat"][i]), float(u["gamma_hat"][i]))
+        om = [o.medium(float(T0[i]), 0.6, float(T0[i]) - 0.02, float(u["kappa_hat"][i]), float(u["gamma_hat"][i]))
               for i in ids]
         r, _, _ = o.run_batch(g, oin, np.arange(len(ids)), om, np.arange(len(ids)), u["seeds"][ids])
         ref[ids] = r
