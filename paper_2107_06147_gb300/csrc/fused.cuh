@@ -209,6 +209,76 @@ template <typename T, int G> __device__ __forceinline__ double slot_norm(SqAcc<T
 // exp(x) and (cos, sin)(pi y): the pi-scaled form has no large-argument reduction path
 __device__ __forceinline__ float k_exp(float x) { return expf(x); }
 __device__ __forceinline__ double k_exp(double x) { return exp(x); }
+__device__ __forceinline__ float k_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double k_expm1(double x) { return expm1(x); }
+
+// f1 = exp(a) exp(i pi y) - 1, the deviation from 1 of a dynamic factor, for a <= 0 (also returns
+// exp(a) - 1).
+// FP32: truncated Taylor series at 0 -- exp(a) - 1 to degree 8 for a >= -1/2 (truncation below
+// |a|^9/9! <= 5.4e-9), sin(t) to degree 9 and cos(t) - 1 to degree 10 in t = pi y for |t| <= 1
+// (truncation below 2.8e-8 and 2.1e-9) -- each accurate relative to the small quantity it returns;
+// outside those ranges (large r, where |f1| is no longer small) the library functions.
+// FP64: expm1 and the half-angle sine and cosine.
+template <typename T> struct Dyn;
+// the rare points outside the series' ranges, kept out of line so the hot loop stays small
+static __device__ __noinline__ void dyn_far(float a, float y, float *em1, float *s, float *cm1)
+{
+    *em1 = expf(a) - 1.0f;
+    float sh, ch;
+    sincospif(0.5f * y, &sh, &ch);
+    *s = 2.0f * sh * ch;
+    *cm1 = -2.0f * sh * sh;
+}
+
+template <> struct Dyn<float> {
+    static __device__ __forceinline__ void f1(float a, float y, float *fr, float *fi, float *e)
+    {
+        float em1, s, cm1;
+        const float t = 3.14159265358979f * y;
+        if (a >= -0.5f && fabsf(t) <= 1.0f) {
+            float p = 1.0f / 40320.0f;
+            p = fmaf(p, a, 1.0f / 5040.0f);
+            p = fmaf(p, a, 1.0f / 720.0f);
+            p = fmaf(p, a, 1.0f / 120.0f);
+            p = fmaf(p, a, 1.0f / 24.0f);
+            p = fmaf(p, a, 1.0f / 6.0f);
+            p = fmaf(p, a, 0.5f);
+            p = fmaf(p, a, 1.0f);
+            em1 = a * p;
+            const float u = t * t;
+            float ps = 1.0f / 362880.0f;
+            ps = fmaf(ps, u, -1.0f / 5040.0f);
+            ps = fmaf(ps, u, 1.0f / 120.0f);
+            ps = fmaf(ps, u, -1.0f / 6.0f);
+            ps = fmaf(ps, u, 1.0f);
+            s = t * ps;
+            float pc = -1.0f / 3628800.0f;
+            pc = fmaf(pc, u, 1.0f / 40320.0f);
+            pc = fmaf(pc, u, -1.0f / 720.0f);
+            pc = fmaf(pc, u, 1.0f / 24.0f);
+            pc = fmaf(pc, u, -0.5f);
+            cm1 = u * pc;
+        } else {
+            dyn_far(a, y, &em1, &s, &cm1);
+        }
+        const float mag = 1.0f + em1;
+        *fr = fmaf(cm1, mag, em1);
+        *fi = s * mag;
+        *e = em1;
+    }
+};
+template <> struct Dyn<double> {
+    static __device__ __forceinline__ void f1(double a, double y, double *fr, double *fi, double *e)
+    {
+        const double em1 = expm1(a);
+        double sh, ch;
+        sincospi(0.5 * y, &sh, &ch);
+        const double mag = 1.0 + em1;
+        *fr = em1 - 2.0 * sh * sh * mag;
+        *fi = 2.0 * sh * ch * mag;
+        *e = em1;
+    }
+};
 __device__ __forceinline__ void k_sincospi(float y, float *s, float *c) { sincospif(y, s, c); }
 __device__ __forceinline__ void k_sincospi(double y, double *s, double *c) { sincospi(y, s, c); }
 
@@ -497,16 +567,21 @@ template <typename T, int N, int V> struct Pointwise {
                 const int j = 2 * k + par;
                 const int p = par ? K::odd_pos(k) : k;
                 const T fj = (T)j;
-                const T mag = k_exp((A * fj) * fj);
-                T s, co;
-                k_sincospi((B * fj) * fj, &s, &co);
+                // the dynamic factor exp(a) exp(i pi y) is close to 1 and changes little from step to
+                // step; it is applied as w + w f1 with f1 its deviation from 1, evaluated so that the
+                // rounding is relative to f1, not to 1 (a rounding of a value next to 1 would repeat
+                // identically every step and add up)
+                T f1r, f1i, em1;
+                Dyn<T>::f1((A * fj) * fj, (B * fj) * fj, &f1r, &f1i, &em1);
+                const T mag = (T)1 + em1;   // |exp(a)|, for the norm weight (working precision suffices)
                 cpx<T> v = buf[p];
                 if (mode == 1) {
                     // exp(2 er_a r^2) = mag * exp((er_a - er_b) r^2), the second factor ~ 1 + 1e-4
                     const T z = (D * fj) * fj;
                     acc.add_w(v, mag * ((T)1 + z * ((T)1 + z * ((T)0.5 + z * (T)(1.0 / 6.0)))));
                 }
-                v = PR::mul(v, stat(tb, tab, c, l, j, mode == 1)) * mk(mag * co, mag * s);
+                const cpx<T> w = PR::mul(v, stat(tb, tab, c, l, j, mode == 1));
+                v = mk(w.x + (w.x * f1r - w.y * f1i), w.y + (w.x * f1i + w.y * f1r));
                 if (mode == 2) acc.add_w(v, (T)1);
                 buf[p] = v;
             }
@@ -552,6 +627,24 @@ template <typename T, int N, int V> struct Pointwise {
             }
         }
         return slot_norm<T, G>(acc, red);
+    }
+
+    // Undoes the start half-step applied by a mode-1 factor, x <- conj(stat1(c,l)) exp(A j^2 + i pi B j^2) x
+    // with A = -er_b dr^2 and B = -ei_b dr^2 / pi: the end-of-step state of a trajectory that stops
+    // at a jump cap.
+    static __device__ void undo_start(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, T A, T B)
+    {
+        for (int k = g; k < N / 2; k += G) {
+            for (int par = 0; par < 2; ++par) {
+                const int j = 2 * k + par;
+                const int p = par ? K::odd_pos(k) : k;
+                const T fj = (T)j, j2 = fj * fj;
+                T sn, cs;
+                k_sincospi(B * j2, &sn, &cs);
+                const T m = k_exp(A * j2);
+                buf[p] = PR::mul(buf[p], PR::conj(stat(tb, tb.statV, c, l, j, false))) * mk(m * cs, m * sn);
+            }
+        }
     }
 
     // x <- x * r_j * f
@@ -693,20 +786,27 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             if (!a.nojump) {
                 if (fabs(n2 - thr) < BORDER_EPS) flags |= QTRAJ_F_BORDERLINE;
                 if (n2 <= thr) {
-                    if (tb.max_jumps >= 0 && nj >= tb.max_jumps) {
-                        flags |= QTRAJ_F_MAXJUMPS;
-                        ended = 1;
-                        break;
-                    }
+                    // a trajectory stopped by a cap keeps its end-of-step state
+                    const bool cap_j = tb.max_jumps >= 0 && nj >= tb.max_jumps;
                     const int l_new = (dw.ul < (double)l / (2.0 * l + 1.0)) ? l - 1 : l + 1;
                     const int c_new = (c == 1 && dw.uc < tb.p_os) ? 0 : 1;
-                    if (fj < 0) fj = n;
-                    if (tb.l_cap >= 0 && l_new > tb.l_cap) {
-                        flags |= QTRAJ_F_LCAP;
-                        l = l_new; c = c_new; ++nj;
+                    const bool cap_l = !cap_j && tb.l_cap >= 0 && l_new > tb.l_cap;
+                    if (cap_j || cap_l) {
+                        if (!last) {
+                            __syncthreads();
+                            PW::undo_start(buf, tb, g, c, l, -(T)md.erj[c] * T3b, -(T)md.eij[c] * T3b);
+                        }
                         ended = 1;
+                        if (cap_j) {
+                            flags |= QTRAJ_F_MAXJUMPS;
+                        } else {
+                            flags |= QTRAJ_F_LCAP;
+                            if (fj < 0) fj = n;
+                            l = l_new; c = c_new; ++nj;
+                        }
                         break;
                     }
+                    if (fj < 0) fj = n;
                     // r times the end-of-step state, renormalised; the start half-step already applied
                     // is turned into the new colour's and l's
                     __syncthreads();

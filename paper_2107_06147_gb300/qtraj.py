@@ -177,14 +177,15 @@ class Engine:
         if workspace is None:
             workspace = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
         self.ws = workspace
-        ptr = workspace.data_ptr()
-        ptr = (ptr + 255) & ~255
+        base = workspace.data_ptr()
+        ptr = (base + 255) & ~255
+        have = max(0, workspace.numel() * workspace.element_size() - (ptr - base))
         arr = (InitSpec * len(specs))(*specs)
         idx = None
         if spec_idx is not None:
             self._spec_idx = np.ascontiguousarray(spec_idx, dtype=np.int32)
             idx = self._spec_idx.ctypes.data_as(C.POINTER(C.c_int))
-        _check(self.lib.qtraj_init(self.ctx, C.c_void_p(ptr), nb, n_traj, arr, len(specs), idx), self.ctx)
+        _check(self.lib.qtraj_init(self.ctx, C.c_void_p(ptr), have, n_traj, arr, len(specs), idx), self.ctx)
         self.n_traj = n_traj
 
     def set_spec_idx(self, spec_idx):
