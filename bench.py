@@ -39,6 +39,9 @@ sys.path.insert(0, ROOT)
 METRIC = "traj-steps/s at N=4096 vs plain FP64 GPU form at stated error; p99 request latency"
 UNIT = "traj-steps/s"
 N_GRID, L_BOX, DT = 4096, 40.0, 0.001
+# DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 171.07
+N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
 def workload_config(batch):
@@ -224,8 +227,15 @@ def run_ours(args):
     alg = algorithmic_flops_per_step(N_GRID)
     achieved = main_steps * alg / (sum(main_ms) / 1e3) / 1e12
     peak = fp32_peak_tflops(kinfo.sm_count)
+    # DRAM bytes of one main launch: the per-trajectory-step figure of the ncu capture of this kernel
+    # (dram__bytes_read.sum + dram__bytes_write.sum over 456 trajectories x 1000 steps, spill
+    # write-back almost all of it) scaled to the launch's trajectory-steps
+    traffic = None
+    if args.precision == "fp32" and args.variant == 0:
+        traffic = round(PROFILED_DRAM_BYTES_PER_TRAJ_STEP * main_steps / args.steps)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_note": "bytes per launch, scaled from a 456-trajectory x 1000-step ncu capture",
                 "flops_per_traj_step": alg, "nominal_fft_equivalent_flops_per_traj_step": nominal_flops_per_step(N_GRID),
                 "peak_note": "FP32 FMA peak from unit counts: SMs x 128 lanes x 2 flops x 2070 MHz (not measured)"}
 
@@ -313,8 +323,11 @@ def oracle_sample(n_traj, prefix_steps=2500, seed_offset=0):
     threads = os.cpu_count() or 1
     g = orc.Grid(N=N_GRID, L=L_BOX, dt=DT, use_rmin=0)
     T0, tau0 = 0.425, 0.6
-    tau_end = tau0 + prefix_steps * DT * 0.1973269804
-    Tf = T0 * (tau0 / tau_end) ** (1.0 / 3.0) * (1 + 1e-9)
+    if prefix_steps >= N_STEPS_FULL:
+        Tf = 0.25
+    else:
+        tau_end = tau0 + prefix_steps * DT * 0.1973269804
+        Tf = T0 * (tau0 / tau_end) ** (1.0 / 3.0) * (1 + 1e-9)
     m = orc.medium(T0, tau0, Tf, 5.0, 0.0)
     spec = orc.init_spec("gauss", 0.2, 1, 0, 0)
     seeds = np.arange(n_traj, dtype=np.uint64) + seed_offset
@@ -326,11 +339,14 @@ def oracle_sample(n_traj, prefix_steps=2500, seed_offset=0):
 
 
 def cpu_baseline(args):
+    """Two trajectories per host core through the whole Bjorken medium (11,899 steps): ~10-20 s of
+    oracle work on a 16-core host."""
     cores = os.cpu_count() or 1
-    steps, secs, thr = oracle_sample(cores)
+    steps, secs, thr = oracle_sample(2 * cores, prefix_steps=N_STEPS_FULL)
     return {"value": round(steps / secs, 1), "unit": UNIT, "cores": thr, "kind": "oracle",
-            "sample": f"{cores} trajectories (one per core) of the 1S/kappa=5/gamma=0 group, N=4096, "
-                      f"first {steps // cores} steps of the Bjorken medium, plain FP64 C oracle, {secs:.1f} s"}
+            "sample": f"{2 * cores} trajectories (two per core) of the 1S/kappa=5/gamma=0 group, N=4096, "
+                      f"all {steps // (2 * cores)} steps of the Bjorken medium 0.425->0.25 GeV, "
+                      f"plain FP64 C oracle, {secs:.1f} s"}
 
 
 def run_reference(args):
