@@ -422,8 +422,15 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
     ap.add_argument("--profile-steps", type=int, default=1000)
+    ap.add_argument("--precision-study", type=int, default=0, metavar="NTRAJ",
+                    help="paired FP64/FP32 study on NTRAJ trajectories of N=8192, L=80, dt=0.0005 (no timing line)")
     args = ap.parse_args()
     args.batch_given = any(a.startswith("--batch") for a in sys.argv[1:])
+    if args.precision_study:
+        from paper_2107_06147_gb300 import build, inputs, precision
+        build.build()
+        print(json.dumps(precision.run(inputs.precision(n_traj=args.precision_study))))
+        return
     if args.profile_case:
         from paper_2107_06147_gb300 import build
         build.build()

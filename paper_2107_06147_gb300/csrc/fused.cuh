@@ -218,7 +218,7 @@ __device__ __forceinline__ double k_expm1(double x) { return expm1(x); }
 // |a|^9/9! <= 5.4e-9), sin(t) to degree 9 and cos(t) - 1 to degree 10 in t = pi y for |t| <= 1
 // (truncation below 2.8e-8 and 2.1e-9) -- each accurate relative to the small quantity it returns;
 // outside those ranges (large r, where |f1| is no longer small) the library functions.
-// FP64: expm1 and the half-angle sine and cosine.
+// FP64: exp and sincospi; a rounding next to 1 is 1e-16 there and does not matter.
 template <typename T> struct Dyn;
 // the rare points outside the series' ranges, kept out of line so the hot loop stays small
 static __device__ __noinline__ void dyn_far(float a, float y, float *em1, float *s, float *cm1)
@@ -270,13 +270,12 @@ template <> struct Dyn<float> {
 template <> struct Dyn<double> {
     static __device__ __forceinline__ void f1(double a, double y, double *fr, double *fi, double *e)
     {
-        const double em1 = expm1(a);
-        double sh, ch;
-        sincospi(0.5 * y, &sh, &ch);
-        const double mag = 1.0 + em1;
-        *fr = em1 - 2.0 * sh * sh * mag;
-        *fi = 2.0 * sh * ch * mag;
-        *e = em1;
+        const double mag = exp(a);
+        double s, c;
+        sincospi(y, &s, &c);
+        *fr = mag * c - 1.0;
+        *fi = mag * s;
+        *e = mag - 1.0;
     }
 };
 __device__ __forceinline__ void k_sincospi(float y, float *s, float *c) { sincospif(y, s, c); }

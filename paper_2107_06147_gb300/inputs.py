@@ -117,10 +117,12 @@ def headline(n_traj: int = 16384, N: int = 4096) -> Workload:
                     np.arange(n_traj, dtype=np.uint64))
 
 
-def precision(n_traj: int = 4096) -> Workload:
-    """Precision study: N=8192, L=80, dt=0.0005, singlet Gaussian S wave, kappa_hat=5, gamma_hat=0."""
-    return Workload("precision N=8192 L=80 dt=0.0005", GridSpec(8192, 80.0, 0.0005), [GAUSS_1S], [MediumSpec()],
-                    np.zeros(n_traj, np.int32), np.zeros(n_traj, np.int32), np.arange(n_traj, dtype=np.uint64))
+def precision(n_traj: int = 4096, N: int = 8192, L: float = 80.0, dt: float = 0.0005) -> Workload:
+    """Precision study: N=8192, L=80, dt=0.0005, singlet Gaussian S wave, kappa_hat=5, gamma_hat=0,
+    Bjorken 0.425 -> 0.25 GeV (23,797 steps); seeds = trajectory ids."""
+    return Workload(f"precision N={N} L={L:g} dt={dt:g} 1S Gaussian kappa=5 gamma=0", GridSpec(N, L, dt), [GAUSS_1S],
+                    [MediumSpec()], np.zeros(n_traj, np.int32), np.zeros(n_traj, np.int32),
+                    np.arange(n_traj, dtype=np.uint64))
 
 
 def small_parity(N: int = 64, n_traj: int = 16, seed: int = 7) -> Workload:

@@ -328,6 +328,20 @@ def test_uneven_batch_against_oracle(q, precision):
         assert np.abs(obs["surv"].mean(0) - ref["surv"].mean(0)).max() <= FP32_ENSEMBLE_ABS
 
 
+def test_precision_study_small(q):
+    """The paired FP64/FP32 study (precision.run) on a small grid: 256 trajectories of the 1S Gaussian
+    through the whole Bjorken medium (11,899 steps).  FP32 keeps most jump sequences and its ensemble
+    means stay well inside the statistical resolution of the run."""
+    from paper_2107_06147_gb300 import inputs, precision
+    w = inputs.precision(n_traj=256, N=256, L=5.0, dt=0.001)
+    rep = precision.run(w)
+    f = rep["forms"]["fp32"]
+    assert rep["trajectories"] == 256 and rep["steps_per_trajectory"] == 11899
+    assert f["fraction_jump_steps_differ"] < 0.25, f
+    for b in ("1S", "2S", "1P"):
+        assert f["ensemble_mean_abs_error"][b] < max(rep["reference"]["survival_sem"][b], 1e-4), (b, f, rep)
+
+
 def test_nonfinite_input_is_reported(q):
     """A malformed input (an initial Gaussian so narrow that its grid norm is zero) makes the norm
     NaN on the GPU; the trajectory is flagged and qtraj_observables returns QTRAJ_ENONFINITE instead
