@@ -174,6 +174,67 @@ typedef struct {
 qtraj_status qtraj_kernel_info_get(const qtraj_ctx *ctx, qtraj_kernel_info *out);
 
 /* ---------------------------------------------------------------------------------------------
+ * Serving: continuous batching of trajectory requests.  (The paper has no counterpart: its program
+ * evolves one batch per invocation.)
+ *
+ * A server owns, for every grid size N it serves, `slots_per_n` contexts, each with its share of
+ * the caller's workspace, its own non-blocking CUDA stream and a pinned host buffer for results.
+ *   - qtraj_submit queues a request: n trajectory descriptors (grid size, initial state from the
+ *     server's catalogue, medium, Philox seed) under a caller-chosen id.  Host only.
+ *   - qtraj_poll never blocks.  It collects finished launches; admits queued requests first come
+ *     first served while the trajectories admitted and not yet returned stay within
+ *     max_inflight_traj (a request larger than the whole budget is admitted when nothing else is in
+ *     flight); and fills every idle slot with up to waves_per_launch waves (SMs x resident CTAs)
+ *     of trajectories taken in order across the admitted requests of that grid size.  So the
+ *     trajectories of several requests share a launch, a request that arrives while others run
+ *     joins the next launch that frees up, and slots of different grid sizes run concurrently on the
+ *     device.  It writes to done_ids the ids of requests whose last trajectory has finished (at
+ *     most `capacity`; the rest are reported by the next call).
+ *   - qtraj_request_result copies a finished request's n records (in submission order) to host
+ *     memory and forgets the request.
+ * A trajectory's record depends only on its descriptor, never on its launch mates.  Every launch
+ * is the fused form with the rMin shortcut off (launches mix many (state, medium) groups); the
+ * other fields of `params` apply.  Errors: QTRAJ_EINVAL for a grid size not served, a catalogue
+ * index out of range, an invalid medium (as in qtraj_evolve), n <= 0, or an id already queued or
+ * not yet returned (checked in qtraj_submit, before anything is queued); QTRAJ_ECUDA from qtraj_poll
+ * if a launch failed.  One host thread at a time per server.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct qtraj_server qtraj_server;
+
+typedef struct {
+    int N;               /* grid size: one of the server's */
+    int spec;            /* index into the server's initial-state catalogue */
+    qtraj_medium medium; /* this trajectory's medium */
+    uint64_t seed;       /* Philox key (Sec. 3.5 draws) */
+} qtraj_traj_desc;
+
+typedef struct {
+    const int *Ns;                 /* grid sizes served (powers of two, 16..16384); L = N * dr */
+    int n_N;
+    double dr, dt, M;              /* grid spacing (GeV^-1), step (GeV^-1), heavy-quark mass (GeV) */
+    const qtraj_params *params;    /* physics options and precision; form, save_states, use_rmin ignored */
+    const qtraj_init_spec *specs;  /* initial-state catalogue, 1..QTRAJ_SERVER_MAX_SPECS entries */
+    int n_specs;
+    int slots_per_n;               /* contexts per grid size, >= 1 */
+    int waves_per_launch;          /* >= 1 */
+    int64_t max_inflight_traj;     /* admission budget, >= 1 */
+} qtraj_server_config;
+
+#define QTRAJ_SERVER_MAX_SPECS 64
+
+/* Device workspace the server needs (bytes, 256-byte aligned base required). */
+qtraj_status qtraj_server_workspace_bytes(const qtraj_server_config *cfg, size_t *bytes);
+/* Creates the contexts, binds them to d_ws and uploads the catalogue's initial states.  Synchronous. */
+qtraj_status qtraj_server_create(const qtraj_server_config *cfg, void *d_ws, size_t bytes, qtraj_server **out);
+qtraj_status qtraj_submit(qtraj_server *srv, const qtraj_traj_desc *traj, int n, uint64_t request_id);
+qtraj_status qtraj_poll(qtraj_server *srv, uint64_t *done_ids, int capacity, int *n_done);
+qtraj_status qtraj_request_result(qtraj_server *srv, uint64_t request_id, qtraj_obs *out, int n);
+/* Requests queued but not admitted, admitted but not finished, and launches in flight. */
+qtraj_status qtraj_server_counts(const qtraj_server *srv, int *waiting, int *admitted, int *launches_in_flight);
+/* Waits for the launches in flight, then frees everything the server allocated (not d_ws). */
+void qtraj_server_destroy(qtraj_server *srv);
+
+/* ---------------------------------------------------------------------------------------------
  * Evolving without allocating.  (The paper has no counterpart: its program runs on CPUs only.)
  *
  * For callers that cannot allocate at the point of the call -- a service that hands all device

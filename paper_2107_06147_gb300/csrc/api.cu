@@ -10,6 +10,7 @@
 #include <utility>
 #include <vector>
 
+#include "api_internal.h"
 #include "fused_launch.cuh"
 #include "plain.cuh"
 #include "qtraj.h"
@@ -594,6 +595,59 @@ qtraj_status qtraj_observables(qtraj_ctx *c, void *out, int out_is_device, void 
     }
     return QTRAJ_OK;
 }
+
+} // extern "C"
+
+namespace qt {
+qtraj_status api_fail(qtraj_status st, const char *msg)
+{
+    g_err = msg;
+    return st;
+}
+
+void api_clear_error() { g_err.clear(); }
+
+qtraj_status obs_to_host_async(qtraj_ctx *c, void *host, cudaStream_t s)
+{
+    if (!c || !host) return fail(QTRAJ_EINVAL, "null argument");
+    if (!c->evolved) return fail(QTRAJ_EINVAL, "no evolve has been enqueued");
+    const size_t bytes = sizeof(qtraj_obs) * c->last_batch;
+    if (bytes) CK(cudaMemcpyAsync(host, c->ws + c->off_obs, bytes, cudaMemcpyDeviceToHost, s));
+    return QTRAJ_OK;
+}
+
+qtraj_status reserve_media(qtraj_ctx *c, int n)
+{
+    if (!c || n <= 0) return fail(QTRAJ_EINVAL, "bad argument");
+    if (n > c->media_cap) {
+        CK(cudaDeviceSynchronize());
+        free_typed(c->media);
+        CK(cudaMalloc(&c->media, sizeof(MediumDev) * n));
+        c->media_cap = n;
+    }
+    // the pinned staging of an evolve of n trajectories with up to n media and n groups
+    const size_t need = align256(sizeof(MediumDev) * n) + 2 * align256(sizeof(TrajDev) * n) + 256;
+    if (need > c->h_stage_bytes) {
+        CK(cudaDeviceSynchronize());
+        if (c->h_stage) CK(cudaFreeHost(c->h_stage));
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        CK(cudaMallocHost(&c->h_stage, need));
+        c->h_stage_bytes = need;
+    }
+    return QTRAJ_OK;
+}
+
+const char *medium_problem(const qtraj_medium &q)
+{
+    if (q.kind != 0) return "only kind 0 (Bjorken) is supported";
+    if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return "T0, tau0, Tf must be positive";
+    if (!(q.kappa_hat >= 0) || !(q.gamma_hat <= 0)) return "kappa_hat >= 0 and gamma_hat <= 0 required";
+    return nullptr;
+}
+} // namespace qt
+
+extern "C" {
 
 qtraj_status qtraj_states(qtraj_ctx *c, void *out, int out_is_device, void *stream)
 {

@@ -54,6 +54,22 @@ class KernelInfo(C.Structure):
                 ("regs_per_thread", C.c_int), ("radix", C.c_int), ("sm_count", C.c_int)]
 
 
+class TrajDesc(C.Structure):
+    _fields_ = [("N", C.c_int), ("spec", C.c_int), ("medium", Medium), ("seed", C.c_uint64)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("Ns", C.POINTER(C.c_int)), ("n_N", C.c_int), ("dr", C.c_double), ("dt", C.c_double),
+                ("M", C.c_double), ("params", C.POINTER(Params)), ("specs", C.POINTER(InitSpec)), ("n_specs", C.c_int),
+                ("slots_per_n", C.c_int), ("waves_per_launch", C.c_int), ("max_inflight_traj", C.c_int64)]
+
+
+# qtraj_traj_desc as a numpy record, to build large requests without a Python loop
+TRAJ_DESC_DTYPE = np.dtype([("N", "<i4"), ("spec", "<i4"), ("kind", "<i4"), ("_pad", "<i4"), ("T0", "<f8"),
+                            ("tau0", "<f8"), ("Tf", "<f8"), ("kappa_hat", "<f8"), ("gamma_hat", "<f8"),
+                            ("seed", "<u8")])
+assert TRAJ_DESC_DTYPE.itemsize == C.sizeof(TrajDesc) == 64
+
 OBS_DTYPE = np.dtype([("surv", "<f8", NBASIS), ("ov_re", "<f8", NBASIS), ("ov_im", "<f8", NBASIS),
                       ("norm2", "<f8"), ("r0", "<f8"), ("l", "<i4"), ("color", "<i4"), ("n_jumps", "<i4"),
                       ("n_steps_exec", "<i4"), ("flags", "<i4"), ("first_jump_step", "<i4")])
@@ -75,6 +91,13 @@ _PROTOS = {
     "qtraj_nojump_results": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "qtraj_last_run_stats": (C.c_int, [C.c_void_p, C.POINTER(RunStats)]),
     "qtraj_kernel_info_get": (C.c_int, [C.c_void_p, C.POINTER(KernelInfo)]),
+    "qtraj_server_workspace_bytes": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_size_t)]),
+    "qtraj_server_create": (C.c_int, [C.POINTER(ServerConfig), C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
+    "qtraj_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_uint64]),
+    "qtraj_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_int, C.POINTER(C.c_int)]),
+    "qtraj_request_result": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int]),
+    "qtraj_server_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "qtraj_server_destroy": (None, [C.c_void_p]),
     "qtraj_evolve_static": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(InitSpec), C.c_int, C.POINTER(C.c_int),
                                       C.POINTER(Medium), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint64),
                                       C.c_void_p, C.c_void_p]),

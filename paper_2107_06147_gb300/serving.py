@@ -1,23 +1,23 @@
-"""Continuous-batching request loop over libqtraj.
+"""Continuous batching of trajectory requests: a thin binding of libqtraj's server.
 
-A request asks for `ntraj` trajectories of one initial state (1S Gaussian, Coulomb 2S or 1P Gaussian)
-in one Bjorken medium (T0, kappa_hat, gamma_hat) on an N-point grid.  The server keeps, for every
-grid size N it serves, a few engine slots (a libqtraj context with its own workspace and CUDA
-stream).  Whenever a slot is free, the scheduler fills it with up to one full wave of trajectories
-taken first-come-first-served from the pending requests of that N -- trajectories of several
-requests share a launch, and a request that arrives while others run joins the next launch that
-frees up.  Slots of different N (and several slots of one N) run concurrently on separate streams, so
-their work overlaps on the device.  Admission is bounded by a budget of trajectories in flight.
+The scheduler is native (include/qtraj.h, "Serving"; csrc/serve.cu): for every grid size N the
+server keeps a few engine slots (a context with its share of the workspace, its own CUDA stream and
+a pinned result buffer).  qtraj_poll never blocks: it retires finished launches, admits queued
+requests first come first served within a budget of trajectories in flight, and fills every idle
+slot with up to `wave_mult` waves of trajectories taken in order across the admitted requests of that
+N -- trajectories of several requests share a launch, a request that arrives while others run joins
+the next launch that frees up, and slots of different N run concurrently on the device.
 
 Each trajectory's result depends only on its own inputs (initial state, medium, seed), never on the
-batch it shares a launch with, so a request's results are the same alone and in the mix.
+launch it shares, so a request's results are the same alone and in the mix.
 
-Arithmetic runs in libqtraj; this module only schedules (host bookkeeping, torch streams and events).
+This module marshals requests into trajectory descriptors, holds the workspace (a torch tensor), and
+replays timed request streams; it does no arithmetic of the method.
 """
 from __future__ import annotations
 
+import ctypes as C
 import time
-from collections import deque
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -33,7 +33,7 @@ INIT_SPECS = (qtraj.init_spec("gauss", 0.2, 1, 0, 0),     # 1S-like Gaussian S w
 class Request:
     rid: int
     N: int
-    init: int            # index into INIT_SPECS
+    init: int            # index into the server's initial-state catalogue (INIT_SPECS by default)
     T0: float
     kappa_hat: float
     gamma_hat: float
@@ -41,120 +41,74 @@ class Request:
     seed0: int
     Tf: float = 0.25
     arrival: float = 0.0
-    admitted: float = -1.0
     done_time: float = -1.0
-    next_traj: int = 0   # trajectories handed to launches so far
-    n_done: int = 0
     obs: np.ndarray = field(default=None, repr=False)
 
-    def medium(self):
-        return qtraj.medium(self.T0, 0.6, self.Tf, self.kappa_hat, self.gamma_hat)
-
-
-class _Slot:
-    def __init__(self, N, L, dt, precision, cap, device):
-        import torch
-        self.eng = qtraj.Engine(qtraj.Config(N=N, L=L, dt=dt, precision=precision, use_rmin=0))
-        self.cap = cap
-        self.eng.init(list(INIT_SPECS), cap, spec_idx=np.zeros(cap, np.int32))
-        self.stream = torch.cuda.Stream(device=device)
-        self.event = torch.cuda.Event()
-        self.busy = False
-        self.parts = []      # (request, first trajectory, count) in launch order
+    def descriptors(self) -> np.ndarray:
+        """The request's trajectories: seeds seed0 .. seed0 + ntraj - 1, all on grid N."""
+        d = np.zeros(self.ntraj, dtype=qtraj.TRAJ_DESC_DTYPE)
+        d["N"] = self.N
+        d["spec"] = self.init
+        d["T0"], d["tau0"], d["Tf"] = self.T0, 0.6, self.Tf
+        d["kappa_hat"], d["gamma_hat"] = self.kappa_hat, self.gamma_hat
+        d["seed"] = np.uint64(self.seed0) + np.arange(self.ntraj, dtype=np.uint64)
+        return d
 
 
 class Server:
-    """Per-N engine slots; see the module docstring."""
+    """A libqtraj server over the grid sizes Ns (L = N dr); see the module docstring."""
 
     def __init__(self, Ns=(1024, 2048, 4096, 8192, 16384), slots_per_n: int = 2, precision=qtraj.FP32,
-                 max_inflight_traj: int = 1 << 20, dr: float = 5.0 / 512, dt: float = 0.001, wave_mult: int = 1):
+                 max_inflight_traj: int = 1 << 20, dr: float = 5.0 / 512, dt: float = 0.001, wave_mult: int = 1,
+                 specs=INIT_SPECS, cfg: qtraj.Config | None = None):
         import torch
-        self.device = torch.cuda.current_device()
-        self.slots = {}
-        self.pending = {}
-        self.max_inflight = max_inflight_traj
-        self.inflight = 0
-        for N in Ns:
-            probe = qtraj.Engine(qtraj.Config(N=N, L=N * dr, dt=dt, precision=precision, use_rmin=0))
-            ki = probe.kernel_info()
-            probe.close()
-            cap = ki.sm_count * ki.ctas_per_sm * wave_mult
-            self.slots[N] = [_Slot(N, N * dr, dt, precision, cap, self.device) for _ in range(slots_per_n)]
-            self.pending[N] = deque()
-        self.waiting = deque()    # arrived, not yet admitted
+        self.lib = qtraj.load()
+        base = cfg or qtraj.Config(precision=precision)
+        self._params = base.params()
+        self._Ns = (C.c_int * len(Ns))(*Ns)
+        self._specs = (qtraj.InitSpec * len(specs))(*specs)
+        self._cfg = qtraj.ServerConfig(self._Ns, len(Ns), dr, dt, base.M, C.pointer(self._params), self._specs,
+                                       len(specs), slots_per_n, wave_mult, max_inflight_traj)
+        nb = C.c_size_t()
+        qtraj._check(self.lib.qtraj_server_workspace_bytes(C.byref(self._cfg), C.byref(nb)))
+        self.ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        ptr = (self.ws.data_ptr() + 255) & ~255
+        h = C.c_void_p()
+        qtraj._check(self.lib.qtraj_server_create(C.byref(self._cfg), C.c_void_p(ptr), nb.value, C.byref(h)))
+        self.h = h
+        self.requests = {}
         self.completed = []
+        self._ids = (C.c_uint64 * 256)()
 
-    # ------------------------------------------------------------------------------------------
     def submit(self, req: Request, now: float | None = None):
         req.arrival = time.perf_counter() if now is None else now
-        req.obs = np.zeros(req.ntraj, dtype=qtraj.OBS_DTYPE)
-        self.waiting.append(req)
+        d = req.descriptors()
+        qtraj._check(self.lib.qtraj_submit(self.h, C.c_void_p(d.ctypes.data), len(d), req.rid))
+        self.requests[req.rid] = req
 
-    def _admit(self, now):
-        while self.waiting and self.inflight + self.waiting[0].ntraj <= self.max_inflight:
-            r = self.waiting.popleft()
-            r.admitted = now
-            self.inflight += r.ntraj
-            self.pending[r.N].append(r)
-
-    def _launch(self, N, slot):
-        q = self.pending[N]
-        parts, n = [], 0
-        while q and n < slot.cap:
-            r = q[0]
-            take = min(r.ntraj - r.next_traj, slot.cap - n)
-            parts.append((r, r.next_traj, take))
-            r.next_traj += take
-            n += take
-            if r.next_traj == r.ntraj:
-                q.popleft()
-        if n == 0:
-            return False
-        spec_idx = np.concatenate([np.full(c, r.init, np.int32) for r, _, c in parts])
-        media_idx = np.concatenate([np.full(c, i, np.int32) for i, (r, _, c) in enumerate(parts)])
-        seeds = np.concatenate([np.arange(f, f + c, dtype=np.uint64) + np.uint64(r.seed0) for r, f, c in parts])
-        media = [r.medium() for r, _, _ in parts]
-        slot.eng.set_spec_idx(spec_idx)
-        slot.eng.evolve(media, seeds, media_idx, stream=slot.stream)
-        slot.event.record(slot.stream)
-        slot.parts = parts
-        slot.busy = True
-        return True
-
-    def _collect(self, slot, now):
-        obs = slot.eng.observables(stream=slot.stream, check_finite=False)
-        o = 0
-        for r, f, c in slot.parts:
-            r.obs[f:f + c] = obs[o:o + c]
-            o += c
-            r.n_done += c
-            if r.n_done == r.ntraj:
-                r.done_time = now
-                self.inflight -= r.ntraj
-                self.completed.append(r)
-        slot.busy = False
-        slot.parts = []
-
-    def poll(self) -> int:
-        """One scheduling pass: retire finished launches, admit, launch into free slots.  Returns the
-        number of launches in flight."""
+    def poll(self) -> list:
+        """One scheduling pass; returns the requests that finished in it (their .obs filled)."""
+        n = C.c_int()
+        qtraj._check(self.lib.qtraj_poll(self.h, self._ids, len(self._ids), C.byref(n)))
         now = time.perf_counter()
-        for N, slots in self.slots.items():
-            for s in slots:
-                if s.busy and s.event.query():
-                    self._collect(s, now)
-        self._admit(now)
-        busy = 0
-        for N, slots in self.slots.items():
-            for s in slots:
-                if not s.busy:
-                    self._launch(N, s)
-                busy += s.busy
-        return busy
+        out = []
+        for i in range(n.value):
+            r = self.requests.pop(int(self._ids[i]))
+            r.obs = np.zeros(r.ntraj, dtype=qtraj.OBS_DTYPE)
+            qtraj._check(self.lib.qtraj_request_result(self.h, r.rid, C.c_void_p(r.obs.ctypes.data), r.ntraj))
+            r.done_time = now
+            self.completed.append(r)
+            out.append(r)
+        return out
+
+    def counts(self):
+        """(requests waiting for admission, admitted and unfinished, launches in flight)."""
+        w, a, l = C.c_int(), C.c_int(), C.c_int()
+        qtraj._check(self.lib.qtraj_server_counts(self.h, C.byref(w), C.byref(a), C.byref(l)))
+        return w.value, a.value, l.value
 
     def idle(self) -> bool:
-        return not self.waiting and all(not q for q in self.pending.values()) and \
-            all(not s.busy for sl in self.slots.values() for s in sl)
+        return not self.requests and self.counts() == (0, 0, 0)
 
     def run_stream(self, requests, arrivals_s, poll_interval_s: float = 0.0005, timeout_s: float = 3600.0):
         """Replays a request stream: request i is submitted at arrivals_s[i] seconds after the start.
@@ -175,9 +129,15 @@ class Server:
         return time.perf_counter() - t0
 
     def close(self):
-        for sl in self.slots.values():
-            for s in sl:
-                s.eng.close()
+        if self.h:
+            self.lib.qtraj_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def latency_stats(reqs):

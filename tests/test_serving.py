@@ -1,72 +1,70 @@
-"""Continuous-batching request loop (paper_2107_06147_gb300.serving).
+"""Continuous batching (libqtraj's server; paper_2107_06147_gb300.serving is its binding).
 
-A request's results must be the same when it is served alone and when it shares launches with
-other requests of the same and of another grid size that arrive while it runs.  Host-side
-scheduling logic (FIFO split of requests into launches, admission budget) is checked on the CPU with
-a fake engine.
+A request's results must be the same when it is served alone and when it shares launches with other
+requests of the same and of another grid size that arrive while it runs, and the same as a direct
+evolve of its trajectories.  Argument checks that run before any CUDA call are tested on the CPU.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
 
-class _FakeEngine:
-    def __init__(self, *a, **k):
-        self.log = []
-
-    def set_spec_idx(self, idx):
-        self.idx = np.array(idx)
-
-    def evolve(self, media, seeds, midx, stream=None):
-        self.log.append((list(seeds), list(midx)))
-        self.seeds = np.array(seeds)
-
-    def observables(self, stream=None, check_finite=True):
-        from paper_2107_06147_gb300 import qtraj
-        o = np.zeros(len(self.seeds), dtype=qtraj.OBS_DTYPE)
-        o["r0"] = self.seeds.astype(np.float64)
-        return o
+def _cfg(qtraj, Ns, specs, **kw):
+    p = qtraj.Config().params()
+    ns = (C.c_int * len(Ns))(*Ns)
+    sp = (qtraj.InitSpec * len(specs))(*specs)
+    c = qtraj.ServerConfig(ns, len(Ns), kw.get("dr", 5.0 / 512), kw.get("dt", 0.001), 4.65, C.pointer(p), sp,
+                           kw.get("n_specs", len(specs)), kw.get("slots", 1), kw.get("waves", 1), kw.get("budget", 100))
+    return c, (p, ns, sp)
 
 
-class _FakeEvent:
-    def record(self, s):
-        pass
+def test_server_arguments_checked_on_host():
+    from paper_2107_06147_gb300 import build, qtraj, serving
+    build.build()
+    lib = qtraj.load()
+    nb = C.c_size_t()
+    for Ns, kw, msg in (((100,), {}, b"power of two"), ((64, 64), {}, b"twice"), ((64,), {"n_specs": 0}, b"n_specs"),
+                        ((64,), {"budget": 0}, b"positive"), ((64,), {"dt": 0.0}, b"positive")):
+        c, keep = _cfg(qtraj, Ns, serving.INIT_SPECS, **kw)
+        assert lib.qtraj_server_workspace_bytes(C.byref(c), C.byref(nb)) == 1
+        assert msg in lib.qtraj_last_error(None)
+    n = C.c_int()
+    assert lib.qtraj_poll(None, None, 0, C.byref(n)) == 1
+    assert lib.qtraj_submit(None, None, 1, 0) == 1
+    # a request's descriptors: one record per trajectory, seeds seed0 + i
+    r = serving.Request(rid=3, N=512, init=2, T0=0.4, kappa_hat=4.0, gamma_hat=-1.0, ntraj=5, seed0=100, Tf=0.3)
+    d = r.descriptors()
+    assert d.dtype.itemsize == C.sizeof(qtraj.TrajDesc) and list(d["seed"]) == [100, 101, 102, 103, 104]
+    assert (d["N"] == 512).all() and (d["spec"] == 2).all() and (d["kind"] == 0).all() and (d["Tf"] == 0.3).all()
 
-    def query(self):
-        return True
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_06147_gb300 import build
+    build.build()
 
 
-def test_scheduler_splits_requests_fifo_and_respects_budget():
-    from paper_2107_06147_gb300 import serving
-    srv = serving.Server.__new__(serving.Server)
-    srv.pending, srv.slots, srv.waiting, srv.completed = {}, {}, serving.deque(), []
-    srv.max_inflight, srv.inflight = 100, 0
-    slot = serving._Slot.__new__(serving._Slot)
-    slot.eng, slot.cap, slot.stream, slot.event, slot.busy, slot.parts = _FakeEngine(), 32, None, _FakeEvent(), False, []
-    srv.slots[64] = [slot]
-    srv.pending[64] = serving.deque()
-    reqs = [serving.Request(rid=i, N=64, init=i % 3, T0=0.4, kappa_hat=4, gamma_hat=-1, ntraj=n, seed0=1000 * i)
-            for i, n in enumerate((20, 30, 70))]
-    for r in reqs:
-        srv.submit(r, now=0.0)
-    srv.poll()                       # admits 20 + 30 (70 would exceed 100), launches 32 of them
-    assert srv.inflight == 50 and len(srv.waiting) == 1
-    seeds, midx = slot.eng.log[-1]
-    assert seeds[:20] == list(range(0, 20)) and seeds[20:] == list(range(1000, 1012))
-    assert midx == [0] * 20 + [1] * 12
-    while not srv.idle():
-        srv.poll()
-    assert [r.n_done for r in reqs] == [20, 30, 70]
-    for r in reqs:                   # every trajectory came back to its own request and slot
-        assert np.array_equal(r.obs["r0"], r.seed0 + np.arange(r.ntraj))
+def _direct(qtraj, N, prec, specs, desc, dr=5.0 / 512, dt=0.001):
+    """The same trajectories through a plain context (fused form, rMin shortcut off)."""
+    import torch
+    e = qtraj.Engine(qtraj.Config(N=N, L=N * dr, dt=dt, precision=prec, use_rmin=0))
+    e.init(list(specs), len(desc), np.ascontiguousarray(desc["spec"], dtype=np.int32))
+    media = [qtraj.medium(float(x["T0"]), float(x["tau0"]), float(x["Tf"]), float(x["kappa_hat"]),
+                          float(x["gamma_hat"])) for x in desc]
+    e.evolve(media, np.ascontiguousarray(desc["seed"]), np.arange(len(desc), dtype=np.int32))
+    o = e.observables(check_finite=False)
+    torch.cuda.synchronize()
+    e.close()
+    return o
 
 
 @pytest.mark.gpu
 def test_request_same_alone_and_in_mix():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2107_06147_gb300 import build, qtraj, serving
-    build.build()
+    _gpu()
+    from paper_2107_06147_gb300 import qtraj, serving
 
     def req(rid, N, init, ntraj, seed0, T0=0.3, kap=4.0, gam=-1.0):
         return serving.Request(rid=rid, N=N, init=init, T0=T0, kappa_hat=kap, gamma_hat=gam, ntraj=ntraj,
@@ -80,8 +78,78 @@ def test_request_same_alone_and_in_mix():
         srv.run_stream(mix, [0.0, 0.001, 0.002, 0.004])
         srv.close()
         a, b = alone.obs, mix[2].obs
-        for f in ("surv", "ov_re", "ov_im", "norm2", "r0"):
-            assert np.array_equal(a[f], b[f]), f
-        for f in ("n_jumps", "first_jump_step", "l", "color", "n_steps_exec", "flags"):
+        for f in qtraj.OBS_DTYPE.names:
             assert np.array_equal(a[f], b[f]), f
         assert all(r.done_time >= r.arrival for r in mix)
+        ref = _direct(qtraj, 512, prec, serving.INIT_SPECS, alone.descriptors())
+        for f in qtraj.OBS_DTYPE.names:
+            assert np.array_equal(a[f], ref[f]), f
+
+
+@pytest.mark.gpu
+def test_budget_fifo_and_mixed_grid_request():
+    """Admission within the budget in arrival order; a request whose trajectories use two grid sizes
+    comes back in submission order, equal to direct evolves of each part."""
+    _gpu()
+    from paper_2107_06147_gb300 import qtraj, serving
+    srv = serving.Server(Ns=(64, 128), slots_per_n=1, precision=qtraj.FP64, wave_mult=1, max_inflight_traj=100)
+    reqs = [serving.Request(rid=10 + i, N=64, init=i % 3, T0=0.35, kappa_hat=5.0, gamma_hat=-0.5, ntraj=n,
+                            seed0=1000 * i, Tf=0.3) for i, n in enumerate((20, 30, 70))]
+    for r in reqs:
+        srv.submit(r)
+    srv.poll()
+    assert srv.counts()[:2] == (1, 2)        # 20 + 30 admitted; 70 would exceed the budget of 100
+    while not srv.idle():
+        srv.poll()
+    for r in reqs:
+        ref = _direct(qtraj, 64, qtraj.FP64, serving.INIT_SPECS, r.descriptors())
+        for f in qtraj.OBS_DTYPE.names:
+            assert np.array_equal(r.obs[f], ref[f]), (r.rid, f)
+    # one request, trajectories alternating between N = 64 and N = 128
+    d = np.concatenate([reqs[0].descriptors(), reqs[1].descriptors()])
+    d["N"][1::2] = 128
+    lib = srv.lib
+    assert lib.qtraj_submit(srv.h, C.c_void_p(d.ctypes.data), len(d), 99) == 0
+    ids, n = (C.c_uint64 * 4)(), C.c_int()
+    got = []
+    while not got:
+        assert lib.qtraj_poll(srv.h, ids, 4, C.byref(n)) == 0
+        got = [int(ids[i]) for i in range(n.value)]
+    assert got == [99]
+    out = np.zeros(len(d), dtype=qtraj.OBS_DTYPE)
+    assert lib.qtraj_request_result(srv.h, 99, C.c_void_p(out.ctypes.data), len(d)) == 0
+    for N in (64, 128):
+        sel = d["N"] == N
+        ref = _direct(qtraj, N, qtraj.FP64, serving.INIT_SPECS, d[sel])
+        for f in qtraj.OBS_DTYPE.names:
+            assert np.array_equal(out[f][sel], ref[f]), (N, f)
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_server_errors():
+    _gpu()
+    from paper_2107_06147_gb300 import qtraj, serving
+    srv = serving.Server(Ns=(64,), slots_per_n=1, precision=qtraj.FP32)
+    lib = srv.lib
+    r = serving.Request(rid=1, N=64, init=0, T0=0.4, kappa_hat=4.0, gamma_hat=-1.0, ntraj=8, seed0=0, Tf=0.38)
+    d = r.descriptors()
+    bad = d.copy()
+    bad["N"][3] = 128
+    assert lib.qtraj_submit(srv.h, C.c_void_p(bad.ctypes.data), len(bad), 5) == 1          # N not served
+    bad = d.copy()
+    bad["spec"][0] = 3
+    assert lib.qtraj_submit(srv.h, C.c_void_p(bad.ctypes.data), len(bad), 5) == 1          # spec outside catalogue
+    bad = d.copy()
+    bad["kappa_hat"][1] = -1.0
+    assert lib.qtraj_submit(srv.h, C.c_void_p(bad.ctypes.data), len(bad), 5) == 1          # invalid medium
+    assert lib.qtraj_submit(srv.h, C.c_void_p(d.ctypes.data), len(d), 5) == 0
+    assert lib.qtraj_submit(srv.h, C.c_void_p(d.ctypes.data), len(d), 5) == 1              # id already queued
+    out = np.zeros(len(d), dtype=qtraj.OBS_DTYPE)
+    assert lib.qtraj_request_result(srv.h, 5, C.c_void_p(out.ctypes.data), len(d)) == 6    # EBUSY: not finished
+    ids, n = (C.c_uint64 * 1)(), C.c_int()
+    while n.value == 0:
+        assert lib.qtraj_poll(srv.h, ids, 1, C.byref(n)) == 0
+    assert lib.qtraj_request_result(srv.h, 5, C.c_void_p(out.ctypes.data), len(d)) == 0
+    assert lib.qtraj_request_result(srv.h, 5, C.c_void_p(out.ctypes.data), len(d)) == 1    # forgotten
+    srv.close()
