@@ -105,6 +105,8 @@ def lib():
         L.oqt_jump_color.restype = C.c_int
         L.oqt_potential_parts.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_double, C.c_double,
                                           C.c_double, C.c_double, cd, cd]
+        L.oqt_kappa_fit.argtypes = [C.c_int, C.c_double]
+        L.oqt_kappa_fit.restype = C.c_double
         _lib = L
     return _lib
 
@@ -240,6 +242,11 @@ def jump_l(l: int, ul: float) -> int:
 def jump_color(g: Grid, color: int, uc: float) -> int:
     p = g.c()
     return lib().oqt_jump_color(C.byref(p), color, uc)
+
+
+def kappa_fit(which: int, T: float) -> float:
+    """kappa_hat(T) of lattice fit `which` (1 central, 2 lower, 3 upper; App. E)."""
+    return lib().oqt_kappa_fit(which, T)
 
 
 def potential(g: Grid, color: int, l: int, T3v: float, kappa_hat: float, gamma_hat: float, r: float) -> complex:

@@ -178,6 +178,26 @@ double oqt_T3(const oqt_params *p, const oqt_medium *m, int n)
     return T * T * T;
 }
 
+/* kappa_hat(T) from the lattice fits of App. E (the potential's parameter kappa = -1, -2, -3 selects the
+ * central, lower and upper fit): kappa_hat = 1 / (a x^{3/2} + b x + c x^{1/2} + d), x = T / T_c with
+ * T_c = 0.155 GeV.  which = 1, 2, 3. */
+double oqt_kappa_fit(int which, double T)
+{
+    static const double coef[3][4] = {{0.00397, -0.08341, 0.98031, -0.51889},
+                                      {0.00712, -0.14262, 1.55601, -0.80712},
+                                      {0.00272, -0.05854, 0.71513, -0.38197}};
+    const double *k = coef[which - 1];
+    double x = T / 0.155;
+    return 1.0 / (k[0] * pow(x, 1.5) + k[1] * x + k[2] * sqrt(x) + k[3]);
+}
+
+/* the kappa_hat a medium uses at temperature cubed T3: its constant, or a lattice fit of T */
+double oqt_kappa_at(const oqt_medium *m, double T3)
+{
+    if (m->kappa_hat >= 0) return m->kappa_hat;
+    return oqt_kappa_fit((int)(-m->kappa_hat), cbrt(T3));
+}
+
 /* V_eff(r) for colour c (0 singlet, 1 octet), angular momentum l, temperature cubed T3.
  * singlet: -C_F a_s/r + gam T^3 r^2/2 - i kap T^3 r^2/2
  * octet  : +a_s/(2 Nc r) + f gam T^3 r^2 - i f kap T^3 r^2,  f = (Nc^2-2)/(4(Nc^2-1)) = 7/32
@@ -342,7 +362,8 @@ void oqt_evolve_nojump(const oqt_params *p, double complex *u, int color, int l,
     oqt_work w;
     oqt_work_init(&w, p);
     for (int n = n0; n < n0 + nsteps; n++) {
-        oqt_load_space_kernel(&w, color, l, oqt_T3(p, m, n), m->kappa_hat, m->gamma_hat);
+        double T3 = oqt_T3(p, m, n);
+        oqt_load_space_kernel(&w, color, l, T3, oqt_kappa_at(m, T3), m->gamma_hat);
         oqt_make_step(&w, u);
         if (norm2_hist) norm2_hist[n - n0] = oqt_norm2(p, u);
     }
@@ -493,7 +514,8 @@ void oqt_trajectory(const oqt_params *p, const oqt_init *in, const oqt_medium *m
     int l = in->l, c = in->color, nj = 0, ns = oqt_n_steps(p, m);
     int ended = 0;
     for (int n = 0; n < ns; n++) {
-        oqt_load_space_kernel(&w, c, l, oqt_T3(p, m, n), m->kappa_hat, m->gamma_hat);
+        double T3 = oqt_T3(p, m, n);
+        oqt_load_space_kernel(&w, c, l, T3, oqt_kappa_at(m, T3), m->gamma_hat);
         oqt_make_step(&w, u);
         o->n_steps_exec = n + 1;
         double n2 = oqt_norm2(p, u);

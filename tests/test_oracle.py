@@ -245,6 +245,46 @@ def test_nonhermitian_decay_rate(oracle_lib):
         assert 3.0 < errs[0] / errs[1] < 5.0            # second order in dt
 
 
+def test_kappa_fits_positive_ordered_decreasing(oracle_lib):
+    """The three lattice fits of kappa_hat(T) (App. E; parameter kappa = -1, -2, -3): positive and
+    decreasing in T over T_c..100 T_c, and the lower-limit fit below the central below the upper-limit
+    fit everywhere there (a swapped or mislabelled coefficient row breaks the order)."""
+    o = oracle_lib
+    T = 0.155 * np.geomspace(1.0, 100.0, 400)
+    k = np.array([[o.kappa_fit(w, t) for t in T] for w in (1, 2, 3)])
+    assert (k > 0).all()
+    assert (np.diff(k, axis=1) < 0).all()
+    assert (k[1] < k[0]).all() and (k[0] < k[2]).all()
+
+
+@pytest.mark.parametrize("which", [1, 2, 3])
+def test_kappa_fit_medium_decays_with_kappa_of_T(oracle_lib, which):
+    """A medium with kappa = -which evolves with Gamma = kappa_hat(T_n) T_n^3 r^2 at step n: the
+    centred decay rate of the norm matches <Gamma> with the fit evaluated at the temperature of that
+    time, early and late in a Bjorken medium (where kappa_hat changes by ~30%), and does not match the
+    other time's value."""
+    o = oracle_lib
+    g = o.Grid(N=256, L=10.0, dt=0.001)
+    dr = g.L / g.N
+    r = np.arange(g.N) * dr
+    m = o.medium(T0=0.45, tau0=0.6, Tf=0.3, kappa_hat=float(-which), gamma_hat=-1.0)
+    u = o.initial_state(g, o.init_spec("gauss", 0.6, 1, 0, 0))
+    rates, gams, k = [], [], []
+    n = 0
+    for stop in (200, 6500):
+        u, h = o.evolve_nojump(g, u, 0, 0, m, n, stop - n)
+        _, h1 = o.evolve_nojump(g, u, 0, 0, m, stop, 1)
+        rates.append(-(h1[0] - h[-2]) / (2 * g.dt))
+        T3 = o.T3(g, m, stop)
+        k.append(o.kappa_fit(which, T3 ** (1 / 3)))
+        gams.append(k[-1] * T3 * dr * np.sum(r * r * np.abs(u) ** 2))
+        n = stop
+    for a, b in zip(rates, gams):
+        assert abs(a - b) / b < 5e-3
+    assert k[1] / k[0] > 1.2                                             # kappa_hat really changed ...
+    assert abs(rates[1] / (gams[1] * k[0] / k[1]) - 1) > 0.15            # ... and the early value is wrong late
+
+
 # ------------------------------------------------------------------------------------------------
 # trajectories: waiting-time statistics, shortcut exactness, options
 # ------------------------------------------------------------------------------------------------
