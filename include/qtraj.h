@@ -76,8 +76,11 @@ typedef struct {
 } qtraj_init_spec;
 
 /* Medium seen by a trajectory.  kind 0 = Bjorken T(tau) = T0 (tau0/tau)^{1/3} from tau0 until
- * T < Tf (Sec. 3.4, Table 1); kappa_hat >= 0 and gamma_hat <= 0 are the transport coefficients
- * kappa = kappa_hat T^3, gamma = gamma_hat T^3 of the potential (App. E). */
+ * T < Tf (Sec. 3.4, Table 1); gamma_hat <= 0 and kappa_hat are the transport coefficients
+ * kappa = kappa_hat T^3, gamma = gamma_hat T^3 of the potential (App. E).  kappa_hat >= 0 is a
+ * constant; kappa_hat = -1, -2, -3 selects the central, lower or upper lattice fit
+ * kappa_hat(T) = 1 / (a x^{3/2} + b x + c x^{1/2} + d), x = T / T_c, T_c = 0.155 GeV (App. E, the
+ * paper's parameter kappa), evaluated at T(tau_n) every step; a fit requires Tf >= T_c. */
 typedef struct {
     int kind;
     double T0, tau0, Tf;

@@ -251,6 +251,46 @@ int medium_steps(double dt, const qtraj_medium &m)
     return (int)s;
 }
 
+// kappa_hat of a medium: >= 0 a constant; -1, -2, -3 the central, lower, upper lattice fit of
+// kappa_hat(T) (App. E; the fits stay positive from T_c = 0.155 GeV up, so Tf >= T_c is required)
+int kappa_fit_index(double k)
+{
+    return k == -1.0 ? 1 : k == -2.0 ? 2 : k == -3.0 ? 3 : 0;
+}
+
+const char *medium_check(const qtraj_medium &q)
+{
+    if (q.kind != 0) return "only kind 0 (Bjorken) is supported";
+    if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return "T0, tau0, Tf must be positive";
+    if (!(q.gamma_hat <= 0)) return "gamma_hat <= 0 required";
+    if (kappa_fit_index(q.kappa_hat) != 0) {
+        if (!(q.Tf >= 0.155)) return "a kappa_hat lattice fit needs Tf >= T_c = 0.155 GeV";
+    } else if (!(q.kappa_hat >= 0)) {
+        return "kappa_hat >= 0, or -1/-2/-3 for a lattice fit, required";
+    }
+    return nullptr;
+}
+
+// the device record of a medium on a context's grid
+MediumDev encode_medium(const qtraj_ctx *c, const qtraj_medium &q)
+{
+    MediumDev d{};
+    const double Nc = c->p.Nc;
+    d.A = q.T0 * q.T0 * q.T0 * q.tau0;
+    d.tau0 = q.tau0;
+    d.dtau = c->dt * HBARC;
+    d.kfit = kappa_fit_index(q.kappa_hat);
+    const double kap = d.kfit ? 1.0 : q.kappa_hat;
+    for (int col = 0; col < 2; ++col) {
+        const double f = col == 0 ? 0.5 : (Nc * Nc - 2.0) / (4.0 * (Nc * Nc - 1.0));
+        d.er[col] = -f * kap * c->dt * 0.5;
+        d.ei[col] = -f * q.gamma_hat * c->dt * 0.5;
+        d.erj[col] = d.er[col] * c->dr * c->dr;
+        d.eij[col] = d.ei[col] * c->dr * c->dr / PI;
+    }
+    return d;
+}
+
 } // namespace
 
 extern "C" {
@@ -445,24 +485,11 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
 
     std::vector<MediumDev> md(n_media);
     std::vector<int> steps(n_media);
-    const double Nc = c->p.Nc;
     for (int m = 0; m < n_media; ++m) {
         const qtraj_medium &q = media[m];
-        if (q.kind != 0) return fail(QTRAJ_EINVAL, "medium %d: only kind 0 (Bjorken) is supported", m);
-        if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return fail(QTRAJ_EINVAL, "medium %d: T0, tau0, Tf > 0", m);
-        if (!(q.kappa_hat >= 0) || !(q.gamma_hat <= 0))
-            return fail(QTRAJ_EINVAL, "medium %d: kappa_hat >= 0 and gamma_hat <= 0 required", m);
+        if (const char *why = medium_check(q)) return fail(QTRAJ_EINVAL, "medium %d: %s", m, why);
         steps[m] = medium_steps(c->dt, q);
-        md[m].A = q.T0 * q.T0 * q.T0 * q.tau0;
-        md[m].tau0 = q.tau0;
-        md[m].dtau = c->dt * HBARC;
-        for (int col = 0; col < 2; ++col) {
-            const double f = col == 0 ? 0.5 : (Nc * Nc - 2.0) / (4.0 * (Nc * Nc - 1.0));
-            md[m].er[col] = -f * q.kappa_hat * c->dt * 0.5;
-            md[m].ei[col] = -f * q.gamma_hat * c->dt * 0.5;
-            md[m].erj[col] = md[m].er[col] * c->dr * c->dr;
-            md[m].eij[col] = md[m].ei[col] * c->dr * c->dr / PI;
-        }
+        md[m] = encode_medium(c, q);
     }
     std::vector<TrajDev> tr(batch);
     std::map<std::pair<int, int>, int> gmap;
@@ -638,13 +665,7 @@ qtraj_status reserve_media(qtraj_ctx *c, int n)
     return QTRAJ_OK;
 }
 
-const char *medium_problem(const qtraj_medium &q)
-{
-    if (q.kind != 0) return "only kind 0 (Bjorken) is supported";
-    if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return "T0, tau0, Tf must be positive";
-    if (!(q.kappa_hat >= 0) || !(q.gamma_hat <= 0)) return "kappa_hat >= 0 and gamma_hat <= 0 required";
-    return nullptr;
-}
+const char *medium_problem(const qtraj_medium &q) { return medium_check(q); }
 } // namespace qt
 
 extern "C" {
@@ -875,26 +896,12 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
             h.ov0[(s * NBASIS + b) * 2 + 1] = 0.0;
         }
     }
-    const double Nc = c->p.Nc;
     int steps[ST_MAX_MEDIA];
     for (int m = 0; m < n_media; ++m) {
         const qtraj_medium &q = media[m];
-        if (q.kind != 0) return fail(QTRAJ_EINVAL, "medium %d: only kind 0 (Bjorken) is supported", m);
-        if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return fail(QTRAJ_EINVAL, "medium %d: T0, tau0, Tf > 0", m);
-        if (!(q.kappa_hat >= 0) || !(q.gamma_hat <= 0))
-            return fail(QTRAJ_EINVAL, "medium %d: kappa_hat >= 0 and gamma_hat <= 0 required", m);
+        if (const char *why = medium_check(q)) return fail(QTRAJ_EINVAL, "medium %d: %s", m, why);
         steps[m] = medium_steps(c->dt, q);
-        MediumDev &d = h.media[m];
-        d.A = q.T0 * q.T0 * q.T0 * q.tau0;
-        d.tau0 = q.tau0;
-        d.dtau = c->dt * HBARC;
-        for (int col = 0; col < 2; ++col) {
-            const double f = col == 0 ? 0.5 : (Nc * Nc - 2.0) / (4.0 * (Nc * Nc - 1.0));
-            d.er[col] = -f * q.kappa_hat * c->dt * 0.5;
-            d.ei[col] = -f * q.gamma_hat * c->dt * 0.5;
-            d.erj[col] = d.er[col] * c->dr * c->dr;
-            d.eij[col] = d.ei[col] * c->dr * c->dr / PI;
-        }
+        h.media[m] = encode_medium(c, q);
     }
     for (int i = 0; i < n_specs * n_media; ++i) g_static_pair_group[i] = -1;
     int n_groups = 0;

@@ -759,23 +759,25 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         // per-step scalars in the working precision: T^3 = A / (tau0 + n dtau)
         const T mA = (T)md.A, mtau0 = (T)md.tau0, mdtau = (T)md.dtau;
         T T3b = mA / mtau0;
+        T K3b = kappa_T3<T>(md.kfit, T3b);   // kappa_hat(T) T^3 when kappa_hat follows a lattice fit
         if (ns > 0) {
             __syncthreads();
-            PW::factor(buf, tb, g, c, l, 0, (T)md.erj[c] * T3b, (T)md.eij[c] * T3b, (T)0, red);
+            PW::factor(buf, tb, g, c, l, 0, (T)md.erj[c] * K3b, (T)md.eij[c] * T3b, (T)0, red);
         }
 
         for (int n = 0; n < ns; ++n) {
-            const T T3a = T3b;
+            const T T3a = T3b, K3a = K3b;
             const bool last = (n + 1 == ns);
             T3b = mA / (mtau0 + (T)(n + 1) * mdtau);
+            K3b = kappa_T3<T>(md.kfit, T3b);
             __syncthreads();
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) K::dst(x, buf, tb, g, wtot, tw1, tw2, h == 1);
             executed = n + 1;
             const T erj = (T)md.erj[c], eij = (T)md.eij[c];
-            const T Tsum = last ? T3a : T3a + T3b;
-            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Tsum, eij * Tsum,
-                                         last ? (T)0 : erj * (T3a - T3b), red) * dr;
+            const T Tsum = last ? T3a : T3a + T3b, Ksum = last ? K3a : K3a + K3b;
+            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Ksum, eij * Tsum,
+                                         last ? (T)0 : erj * (K3a - K3b), red) * dr;
             if (!isfinite(n2)) {
                 flags |= QTRAJ_F_NONFINITE;
                 ended = 1;
@@ -793,7 +795,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                     if (cap_j || cap_l) {
                         if (!last) {
                             __syncthreads();
-                            PW::undo_start(buf, tb, g, c, l, -(T)md.erj[c] * T3b, -(T)md.eij[c] * T3b);
+                            PW::undo_start(buf, tb, g, c, l, -(T)md.erj[c] * K3b, -(T)md.eij[c] * T3b);
                         }
                         ended = 1;
                         if (cap_j) {
@@ -809,9 +811,9 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                     // r times the end-of-step state, renormalised; the start half-step already applied
                     // is turned into the new colour's and l's
                     __syncthreads();
-                    const double dr2 = tb.dr * tb.dr, T3d = (double)T3b;
-                    const T w2 = last ? (T)0 : (T)(-2.0 * md.er[c] * T3d * dr2);
-                    const T dA = last ? (T)0 : (T)((md.er[c_new] - md.er[c]) * T3d * dr2);
+                    const double dr2 = tb.dr * tb.dr, T3d = (double)T3b, K3d = (double)K3b;
+                    const T w2 = last ? (T)0 : (T)(-2.0 * md.er[c] * K3d * dr2);
+                    const T dA = last ? (T)0 : (T)((md.er[c_new] - md.er[c]) * K3d * dr2);
                     const T dB = last ? (T)0 : (T)((md.ei[c_new] - md.ei[c]) * T3d * dr2 * 0.31830988618379067154);
                     const double s = PW::jump_turn(buf, tb, g, c, l, c_new, l_new, last, w2, dA, dB, red) * dr;
                     const double f = 1.0 / sqrt(s);

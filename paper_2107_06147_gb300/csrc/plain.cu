@@ -15,11 +15,12 @@ constexpr int PB = 256; // threads of the per-trajectory kernels
 
 __device__ __forceinline__ double T3_of(const MediumDev &m, int n) { return m.A / (m.tau0 + (double)n * m.dtau); }
 
+// K3 = kappa_T3(md.kfit, T3): the T^3 of the real exponent, times kappa_hat(T) for a fitted medium
 __device__ __forceinline__ cpx<double> space_factor(const Tables<double> &tb, int N, const MediumDev &md, int c, int l,
-                                                    int j, double T3)
+                                                    int j, double T3, double K3)
 {
     const double r = j * tb.dr;
-    return static_factor<double>(tb, N, c, l, j) * dyn_factor(md.er[c] * T3, md.ei[c] * T3, r * r);
+    return static_factor<double>(tb, N, c, l, j) * dyn_factor(md.er[c] * K3, md.ei[c] * T3, r * r);
 }
 
 __device__ __forceinline__ bool running(const PlainState &s, const TrajDev &d, int n)
@@ -112,16 +113,16 @@ __global__ void plain_space_pre(Tables<double> tb, LaunchArgs a, const PlainStat
     const PlainState s = st[b];
     if (!running(s, d, n)) return;
     const MediumDev md = tb.media[d.medium];
-    const double T3 = T3_of(md, n);
+    const double T3 = T3_of(md, n), K3 = kappa_T3<double>(md.kfit, T3);
     const cpx<double> *p = psi + (size_t)b * N;
     cpx<double> *o = y + (size_t)b * N;
     if (q == 0) {
         o[0] = mk(0.0, 0.0);
     } else if (q == N / 2) {
-        o[q] = scale(space_factor(tb, N, md, s.c, s.l, q, T3) * p[q], 2.0);
+        o[q] = scale(space_factor(tb, N, md, s.c, s.l, q, T3, K3) * p[q], 2.0);
     } else {
-        const cpx<double> fa = space_factor(tb, N, md, s.c, s.l, q, T3) * p[q];
-        const cpx<double> fb = space_factor(tb, N, md, s.c, s.l, N - q, T3) * p[N - q];
+        const cpx<double> fa = space_factor(tb, N, md, s.c, s.l, q, T3, K3) * p[q];
+        const cpx<double> fb = space_factor(tb, N, md, s.c, s.l, N - q, T3, K3) * p[N - q];
         const cpx<double> sum = scale(fa + fb, tb.sinpre[q]), dif = scale(fa - fb, 0.5);
         o[q] = sum + dif;
         o[N - q] = sum - dif;
@@ -217,10 +218,10 @@ __global__ void __launch_bounds__(PB) plain_post(Tables<double> tb, LaunchArgs a
         }
     } else {
         const MediumDev md = tb.media[d.medium];
-        const double T3 = T3_of(md, n);
+        const double T3 = T3_of(md, n), K3 = kappa_T3<double>(md.kfit, T3);
         double acc = 0.0;
         for (int j = threadIdx.x; j < N; j += PB) {
-            const cpx<double> f = space_factor(tb, N, md, s.c, s.l, j, T3) * Sb[j];
+            const cpx<double> f = space_factor(tb, N, md, s.c, s.l, j, T3, K3) * Sb[j];
             ob[j] = f;
             acc = fma(f.x, f.x, fma(f.y, f.y, acc));
         }

@@ -267,7 +267,24 @@ struct MediumDev {
     double ei[2];   // -gamma_c dt/2 per colour: the phase of the space kernel is ei*T^3*r^2
     double erj[2];  // er * dr^2: the real exponent is erj * T^3 * j^2 on grid point j
     double eij[2];  // ei * dr^2 / pi: the phase is pi * eij * T^3 * j^2
+    int kfit;       // 0: constant kappa_hat, folded into er/erj; 1, 2, 3: er/erj are per unit kappa_hat
+                    // and T^3 in the real exponent becomes kappa_hat(T) T^3 from lattice fit kfit
 };
+
+// kappa_hat(T) T^3 given T^3: kfit 0 returns T^3 (kappa_hat is folded into the exponent's
+// coefficient); kfit 1, 2, 3 multiply by the central, lower or upper lattice fit of the Munich
+// potential (App. E), kappa_hat = 1 / (a x^{3/2} + b x + c x^{1/2} + d) with x = T / T_c,
+// T_c = 0.155 GeV, evaluated in the working precision once per step.
+template <typename T> __device__ __forceinline__ T kappa_T3(int kfit, T T3)
+{
+    if (kfit == 0) return T3;
+    const T a = kfit == 1 ? (T)0.00397 : kfit == 2 ? (T)0.00712 : (T)0.00272;
+    const T b = kfit == 1 ? (T)-0.08341 : kfit == 2 ? (T)-0.14262 : (T)-0.05854;
+    const T c = kfit == 1 ? (T)0.98031 : kfit == 2 ? (T)1.55601 : (T)0.71513;
+    const T d = kfit == 1 ? (T)-0.51889 : kfit == 2 ? (T)-0.80712 : (T)-0.38197;
+    const T s = sqrt(cbrt(T3) * (T)(1.0 / 0.155));
+    return T3 / (((a * s + b) * s + c) * s + d);
+}
 
 struct TrajDev {
     unsigned long long seed;

@@ -206,6 +206,24 @@ def test_caps(q, opt, precision):
             assert dm.max() <= FP32_ENSEMBLE_ABS * 10, dm
 
 
+@pytest.mark.parametrize("form,precision", [(0, 0), (1, 0), (0, 1)])
+def test_kappa_lattice_fits(q, form, precision):
+    """Media whose kappa_hat follows the central, lower and upper lattice fit of kappa_hat(T)
+    (App. E; kappa = -1, -2, -3) beside one with a constant kappa_hat, in the fused and plain FP64
+    forms and the fused FP32 form."""
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=64, n_traj=32, seed=21)
+    for i, m in enumerate(w.media[:3]):
+        m.kappa_hat = float(-(i + 1))
+    ref, uref = run_oracle(w)
+    assert (ref["n_jumps"] > 0).sum() >= 3
+    obs, u = run_gpu(q, w, precision, form=form)
+    if precision == 0:
+        check_fp64(q, obs, ref, u, uref)
+    else:
+        check_fp32(q, obs, ref, u, uref)
+
+
 @pytest.mark.parametrize("N", [64, 1024])
 def test_fp32_no_jump_norm_has_no_drift(q, N):
     """FP32 against FP64 on the no-jump runs (each a whole medium of 1,500-3,000 steps without a jump):
@@ -372,7 +390,11 @@ def test_workspace_too_small_and_bad_arguments(q):
         e.init([q.init_spec("coulomb", 0.0, 1, 1, 0)], 4)          # l >= n
     e.init([q.init_spec()], 4)
     with pytest.raises(q.QtrajError):
-        e.evolve([q.medium(0.4, 0.6, 0.38, -1.0, 0.0)], np.arange(4, dtype=np.uint64))   # kappa < 0
+        e.evolve([q.medium(0.4, 0.6, 0.38, -0.5, 0.0)], np.arange(4, dtype=np.uint64))   # kappa < 0, not a fit
     with pytest.raises(q.QtrajError):
         e.evolve([q.medium()], np.arange(9, dtype=np.uint64))     # batch > bound trajectories
+    with pytest.raises(q.QtrajError):
+        e.evolve([q.medium(0.4, 0.6, 0.38, -4.0, 0.0)], np.arange(4, dtype=np.uint64))   # no fit -4
+    with pytest.raises(q.QtrajError):
+        e.evolve([q.medium(0.4, 0.6, 0.12, -1.0, 0.0)], np.arange(4, dtype=np.uint64))   # fit below T_c
     e.close()

@@ -141,7 +141,7 @@ def test_server_errors():
     bad["spec"][0] = 3
     assert lib.qtraj_submit(srv.h, C.c_void_p(bad.ctypes.data), len(bad), 5) == 1          # spec outside catalogue
     bad = d.copy()
-    bad["kappa_hat"][1] = -1.0
+    bad["kappa_hat"][1] = -0.5
     assert lib.qtraj_submit(srv.h, C.c_void_p(bad.ctypes.data), len(bad), 5) == 1          # invalid medium
     assert lib.qtraj_submit(srv.h, C.c_void_p(d.ctypes.data), len(d), 5) == 0
     assert lib.qtraj_submit(srv.h, C.c_void_p(d.ctypes.data), len(d), 5) == 1              # id already queued
