@@ -40,7 +40,7 @@ METRIC = "traj-steps/s at N=4096 vs plain FP64 GPU form at stated error; p99 req
 UNIT = "traj-steps/s"
 N_GRID, L_BOX, DT = 4096, 40.0, 0.001
 # DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture
-PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 171.07
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 7.69
 N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
@@ -228,8 +228,8 @@ def run_ours(args):
     achieved = main_steps * alg / (sum(main_ms) / 1e3) / 1e12
     peak = fp32_peak_tflops(kinfo.sm_count)
     # DRAM bytes of one main launch: the per-trajectory-step figure of the ncu capture of this kernel
-    # (dram__bytes_read.sum + dram__bytes_write.sum over 456 trajectories x 1000 steps, spill
-    # write-back almost all of it) scaled to the launch's trajectory-steps
+    # (dram__bytes_read.sum + dram__bytes_write.sum over 456 trajectories x 1000 steps) scaled to the
+    # launch's trajectory-steps
     traffic = None
     if args.precision == "fp32" and args.variant == 0:
         traffic = round(PROFILED_DRAM_BYTES_PER_TRAJ_STEP * main_steps / args.steps)
