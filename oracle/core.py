@@ -37,7 +37,7 @@ class Params(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_double), ("dt", C.c_double), ("M", C.c_double),
                 ("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int),
                 ("max_jumps", C.c_int), ("r_max", C.c_double), ("l_cap", C.c_int),
-                ("use_rmin", C.c_int)]
+                ("use_rmin", C.c_int), ("t_vac", C.c_double)]
 
 
 class Init(C.Structure):
@@ -105,6 +105,9 @@ def lib():
         L.oqt_jump_color.restype = C.c_int
         L.oqt_potential_parts.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_double, C.c_double,
                                           C.c_double, C.c_double, cd, cd]
+        L.oqt_vacuum_steps.argtypes = [C.POINTER(Params)]
+        L.oqt_vacuum_steps.restype = C.c_int
+        L.oqt_start_state.argtypes = [C.POINTER(Params), C.POINTER(Init), cd]
         L.oqt_kappa_fit.argtypes = [C.c_int, C.c_double]
         L.oqt_kappa_fit.restype = C.c_double
         _lib = L
@@ -132,10 +135,11 @@ class Grid:
     r_max: float = 1.0
     l_cap: int = -1
     use_rmin: int = 1
+    t_vac: float = 0.0
 
     def c(self) -> Params:
         return Params(self.N, self.L, self.dt, self.M, self.alpha_s, self.Nc, self.deriv_type,
-                      self.max_jumps, self.r_max, self.l_cap, self.use_rmin)
+                      self.max_jumps, self.r_max, self.l_cap, self.use_rmin, self.t_vac)
 
 
 def init_spec(kind: str = "gauss", width: float = 0.2, n: int = 1, l: int = 0, color: int = 0) -> Init:
@@ -215,6 +219,19 @@ def initial_state(g: Grid, spec: Init) -> np.ndarray:
     p = g.c()
     u = np.zeros(g.N, dtype=np.complex128)
     lib().oqt_initial_state(C.byref(p), C.byref(spec), _dp(u))
+    return u
+
+
+def vacuum_steps(g: Grid) -> int:
+    p = g.c()
+    return lib().oqt_vacuum_steps(C.byref(p))
+
+
+def start_state(g: Grid, spec: Init) -> np.ndarray:
+    """The initial state after the vacuum evolution of g.t_vac (the initial state itself if 0)."""
+    p = g.c()
+    u = np.zeros(g.N, dtype=np.complex128)
+    lib().oqt_start_state(C.byref(p), C.byref(spec), _dp(u))
     return u
 
 

@@ -60,6 +60,7 @@ typedef struct {
     double r_max;     /* 1.0: off */
     int l_cap;        /* < 0: none; a jump to l > l_cap ends the trajectory with zero overlaps */
     int use_rmin;     /* 1: rMin shortcut */
+    double t_vac;     /* vacuum evolution before the medium, GeV^-1 (Table 1: tmed - t0); 0: none */
 } oqt_params;
 
 typedef struct { int kind; double width; int n, l, color; } oqt_init;  /* kind 0 Gaussian, 1 Coulomb */
@@ -354,6 +355,28 @@ void oqt_strang_step(const oqt_params *p, double complex *u, int color, int l, d
     oqt_work_free(&w);
 }
 
+/* steps of the vacuum evolution: t_vac / dt rounded to the nearest integer */
+int oqt_vacuum_steps(const oqt_params *p)
+{
+    if (!(p->t_vac > 0)) return 0;
+    return (int)llround(p->t_vac / p->dt);
+}
+
+/* the state a trajectory starts the medium with (Sec. 3.5 item 3): the initial state, evolved in
+ * vacuum (T = 0: the Coulomb and centrifugal potential of its colour, no imaginary part, no jumps)
+ * for oqt_vacuum_steps(p) Strang steps */
+void oqt_start_state(const oqt_params *p, const oqt_init *in, double complex *u)
+{
+    oqt_initial_state(p, in, u);
+    int nv = oqt_vacuum_steps(p);
+    if (nv == 0) return;
+    oqt_work w;
+    oqt_work_init(&w, p);
+    oqt_load_space_kernel(&w, in->color, in->l, 0.0, 0.0, 0.0);
+    for (int n = 0; n < nv; n++) oqt_make_step(&w, u);
+    oqt_work_free(&w);
+}
+
 /* H_eff evolution without jumps from step n0 for nsteps steps; norm2_hist[i] (optional) is the
  * norm after step n0+i. */
 void oqt_evolve_nojump(const oqt_params *p, double complex *u, int color, int l, const oqt_medium *m,
@@ -399,7 +422,7 @@ static void oqt_basis_init(oqt_basis *b, const oqt_params *p, const oqt_init *in
     double dr = p->L / N;
     b->phi = malloc(sizeof(double) * OQT_NBASIS * N);
     double complex *u0 = malloc(sizeof(double complex) * N);
-    oqt_initial_state(p, in, u0);
+    oqt_start_state(p, in, u0);          /* the survival ratios refer to the state entering the medium */
     for (int s = 0; s < OQT_NBASIS; s++) {
         oqt_eigenstate(p, OQT_BASIS_N[s], OQT_BASIS_L[s], b->phi + (size_t)s * N);
         /* zero unless the initial state is a singlet of the same l; an analytic Coulomb initial
@@ -454,7 +477,7 @@ void oqt_nojump_run(const oqt_params *p, const oqt_init *in, const oqt_medium *m
     oqt_basis b;
     oqt_basis_init(&b, p, in);
     double complex *u = malloc(sizeof(double complex) * N);
-    oqt_initial_state(p, in, u);
+    oqt_start_state(p, in, u);
     int ns = oqt_n_steps(p, m);
     oqt_evolve_nojump(p, u, in->color, in->l, m, 0, ns, NULL);
     memset(o, 0, sizeof(*o));
@@ -482,7 +505,7 @@ void oqt_trajectory(const oqt_params *p, const oqt_init *in, const oqt_medium *m
     o->r0 = r;
     o->l = in->l; o->color = in->color;
     double complex *u = malloc(sizeof(double complex) * N);
-    oqt_initial_state(p, in, u);
+    oqt_start_state(p, in, u);
 
     if (p->use_rmin && nojump) {
         if (fabs(r - nojump->norm2) < OQT_BORDERLINE_EPS) o->flags |= OQT_F_BORDERLINE;

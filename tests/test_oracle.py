@@ -158,6 +158,34 @@ def test_free_gaussian_spreading_closed_form(oracle_lib, dt, steps):
     assert np.linalg.norm(u - ue) / np.linalg.norm(ue) < 1e-10
 
 
+def test_vacuum_evolution_free_gaussian_and_coulomb_phase(oracle_lib):
+    """Vacuum evolution before the medium (Sec. 3.5 item 3; Table 1 tmed - t0): t_vac / dt rounded
+    steps with T = 0.  With alpha_s = 0 the start state of a Gaussian S wave is the spreading free
+    Gaussian at t_vac (closed form); a Coulomb 1S only turns its phase by -E_1 t_vac with
+    E_1 = -M (C_F alpha_s)^2 / 4, keeping its norm."""
+    o = oracle_lib
+    g = o.Grid(N=512, L=20.0, dt=0.001, alpha_s=0.0, t_vac=0.7504)
+    assert o.vacuum_steps(g) == 750
+    D = 0.5
+    r = np.arange(g.N) * (g.L / g.N)
+    spec = o.init_spec("gauss", D, 1, 0, 0)
+    u0 = o.initial_state(g, spec)
+    e0 = _free_gaussian(r, D, 0.0, g.M)
+    c = u0[100] / e0[100]                       # the discrete normalisation, a real constant
+    u = o.start_state(g, spec)
+    ue = c * _free_gaussian(r, D, 750 * g.dt, g.M)
+    assert np.linalg.norm(u - ue) / np.linalg.norm(ue) < 1e-10
+    g = o.Grid(N=2048, L=20.0, dt=0.001, t_vac=2.0)
+    phi = o.eigenstate(g, 1, 0)
+    u = o.start_state(g, o.init_spec("coulomb", 0.0, 1, 0, 0))
+    A = (g.L / g.N) * np.dot(phi, u)
+    E = -np.angle(A) / (o.vacuum_steps(g) * g.dt)
+    E1 = -g.M * (4.0 / 3.0 * 0.3) ** 2 / 4
+    assert abs(E - E1) / abs(E1) < 1e-4 and abs(abs(A) - 1) < 1e-3
+    assert abs(o.norm2(g, u) - 1) < 1e-12
+    assert np.array_equal(o.start_state(o.Grid(N=64, L=2.0), spec), o.initial_state(o.Grid(N=64, L=2.0), spec))
+
+
 def test_derivtype1_matches_three_point_laplacian(oracle_lib):
     """derivType 1 (Sec. 2.4): the kinetic operator is -(u_{j+1} - 2u_j + u_{j-1})/(M dr^2) with
     Dirichlet walls; with V = 0 one step equals exp(-i dt H3) applied with a dense eigen-solver."""
