@@ -62,8 +62,15 @@ typedef struct {
     int form;        /* qtraj_form */
     int save_states; /* 1: keep every final u(r) (FP64) in the workspace for qtraj_states()     */
     int variant;     /* fused kernel variant (FP32, N in {2048, 4096}; elsewhere the same as 0):
-                        0 = radix 16, 512 resident threads per SM; 1 = radix 16, 640;
-                        2 = radix 8, 768; 3 = radix 8, 1024                                        */
+                        0 = radix 16, 512 resident threads per SM (384 at N = 4096); 1 = radix 16,
+                        640; 2 = radix 8, 768; 3 = radix 8, 1024                                   */
+    double t_vacuum; /* >= 0, GeV^-1: vacuum evolution of every initial state before the medium
+                        (Table 1: tmed - t0; Sec. 3.5 item 3): round(t_vacuum / dt) Strang steps
+                        at T = 0 (Coulomb + centrifugal potential of the state's colour, no
+                        imaginary part, no jumps), run once per initial state in qtraj_init, whose
+                        result is the state every trajectory starts the medium with and the
+                        reference of the survival ratios.  Runs in the fused form of the context's
+                        precision, so an FP64 context with t_vacuum > 0 needs N <= 8192. */
 } qtraj_params;
 
 /* Initial state (Table 1, initType/initWidth/initN/initL/initC): kind 0 is the Gaussian

@@ -102,6 +102,7 @@ struct qtraj_ctx {
     double *eig = nullptr;
     double *ic = nullptr, *ov0 = nullptr;
     int *ov0_zero = nullptr, *spec_l = nullptr, *spec_color = nullptr;
+    bool ic_cplx = false;   // ic holds complex states (after a vacuum evolution)
     int n_spec = 0;
     std::vector<qtraj_init_spec> specs;
     std::vector<int> spec_idx;
@@ -229,6 +230,7 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     t.l_cap = c->p.l_cap;
     t.use_rmin = c->p.use_rmin;
     t.r_max = c->p.r_max;
+    t.ic_cplx = c->ic_cplx ? 1 : 0;
     return t;
 }
 
@@ -293,6 +295,79 @@ MediumDev encode_medium(const qtraj_ctx *c, const qtraj_medium &q)
 
 } // namespace
 
+namespace {
+// Evolves every initial state of the context in vacuum for n_vac steps (T = 0: the Coulomb and
+// centrifugal potential of its colour, no imaginary part, no jump test) with the fused kernel of the
+// context's precision, then makes the results the context's (complex) initial states and their
+// overlaps with the Coulomb basis the reference of the survival ratios (Sec. 3.5 item 3).
+qtraj_status vacuum_evolution(qtraj_ctx *c, int n_specs, int n_vac)
+{
+    const int N = c->N;
+    TrajDev *d_tr = nullptr;
+    qtraj_obs *d_obs = nullptr;
+    int *d_ctr = nullptr;
+    double *d_st = nullptr;
+    qtraj_status st = qt::reserve_media(c, 1);
+    if (st != QTRAJ_OK) return st;
+    auto cleanup = [&]() {
+        free_typed(d_tr);
+        free_typed(d_obs);
+        free_typed(d_ctr);
+        free_typed(d_st);
+    };
+    std::vector<TrajDev> tr(n_specs);
+    for (int s = 0; s < n_specs; ++s) tr[s] = TrajDev{0ull, s, 0, n_vac, 0};
+    MediumDev vac{};
+    vac.tau0 = 1.0;   // A = 0: T^3 = 0 at every step; all exponent coefficients 0
+    std::vector<double> states((size_t)n_specs * N * 2);
+    int status = 0;
+    cudaError_t e = cudaMalloc(&d_tr, sizeof(TrajDev) * n_specs);
+    if (e == cudaSuccess) e = cudaMalloc(&d_obs, sizeof(qtraj_obs) * n_specs);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ctr, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&d_st, sizeof(double) * states.size());
+    if (e == cudaSuccess) e = cudaMemcpy(d_tr, tr.data(), sizeof(TrajDev) * n_specs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->media, &vac, sizeof(MediumDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_ctr, 0, 256);
+    if (e == cudaSuccess) {
+        LaunchArgs va{d_tr, n_specs, d_obs, nullptr, d_ctr, d_ctr + 1, d_st, 1};
+        FusedInfo fi;
+        e = c->p.precision == QTRAJ_FP32
+                ? fused_launch_f32(N, tables<float>(c), va, c->sm_count, 0, nullptr, &fi, false, c->p.variant)
+                : fused_launch_f64(N, tables<double>(c), va, c->sm_count, 0, nullptr, &fi, false, c->p.variant);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(states.data(), d_st, sizeof(double) * states.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&status, d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return fail(QTRAJ_ECUDA, "vacuum evolution: %s", cudaGetErrorString(e));
+    if (status & 1) return fail(QTRAJ_ENONFINITE, "vacuum evolution: a norm became non-finite");
+    // the overlaps of the evolved states with the Coulomb basis
+    std::vector<double> ov0((size_t)n_specs * NBASIS * 2, 0.0), phi;
+    std::vector<int> zero((size_t)n_specs * NBASIS);
+    CK(cudaMemcpy(zero.data(), c->ov0_zero, sizeof(int) * zero.size(), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < NBASIS; ++b) {
+        coulomb_u(N, c->dr, c->a0, BASIS_N[b], BASIS_L[b], phi);
+        for (int s = 0; s < n_specs; ++s) {
+            if (zero[(size_t)s * NBASIS + b]) continue;
+            const double *u = states.data() + (size_t)s * N * 2;
+            double re = 0.0, im = 0.0;
+            for (int j = 1; j < N; ++j) {
+                re += phi[j] * u[2 * j];
+                im += phi[j] * u[2 * j + 1];
+            }
+            ov0[((size_t)s * NBASIS + b) * 2] = re * c->dr;
+            ov0[((size_t)s * NBASIS + b) * 2 + 1] = im * c->dr;
+        }
+    }
+    free_typed(c->ic);
+    CK(cudaMalloc(&c->ic, sizeof(double) * states.size()));
+    CK(cudaMemcpy(c->ic, states.data(), sizeof(double) * states.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->ov0, ov0.data(), sizeof(double) * ov0.size(), cudaMemcpyHostToDevice));
+    c->ic_cplx = true;
+    return QTRAJ_OK;
+}
+} // namespace
+
 extern "C" {
 
 const char *qtraj_last_error(const qtraj_ctx *) { return g_err.c_str(); }
@@ -314,6 +389,9 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     if (p.variant < 0 || p.variant > 3) return fail(QTRAJ_EINVAL, "variant must be in 0..3");
     if (p.form == QTRAJ_FUSED && p.precision == QTRAJ_FP64 && N > 8192)
         return fail(QTRAJ_EINVAL, "the fused FP64 form supports N <= 8192");
+    if (!(p.t_vacuum >= 0) || !std::isfinite(p.t_vacuum)) return fail(QTRAJ_EINVAL, "t_vacuum must be finite and >= 0");
+    if (p.t_vacuum > 0 && p.precision == QTRAJ_FP64 && N > 8192)
+        return fail(QTRAJ_EINVAL, "the vacuum evolution runs in the fused form: FP64 needs N <= 8192");
 
     qtraj_ctx *c = new qtraj_ctx();
     c->N = N;
@@ -437,6 +515,7 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
     CK(cudaMalloc(&c->spec_l, sizeof(int) * n_specs));
     CK(cudaMalloc(&c->spec_color, sizeof(int) * n_specs));
     CK(cudaMemcpy(c->ic, ic.data(), sizeof(double) * ic.size(), cudaMemcpyHostToDevice));
+    c->ic_cplx = false;
     CK(cudaMemcpy(c->ov0, ov0.data(), sizeof(double) * ov0.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->ov0_zero, zero.data(), sizeof(int) * zero.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->spec_l, sl.data(), sizeof(int) * n_specs, cudaMemcpyHostToDevice));
@@ -455,6 +534,8 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
     c->off_states = Lw.states;
     c->off_plain = Lw.plain;
     c->evolved = false;
+    const int n_vac = c->p.t_vacuum > 0 ? (int)std::llround(c->p.t_vacuum / c->dt) : 0;
+    if (n_vac > 0) return vacuum_evolution(c, n_specs, n_vac);
     return QTRAJ_OK;
 }
 
@@ -856,6 +937,7 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
     g_err.clear();
     if (!c || !specs || !media || !seeds || !d_out) return fail(QTRAJ_EINVAL, "null argument");
     if (c->p.form != QTRAJ_FUSED) return fail(QTRAJ_EINVAL, "qtraj_evolve_static runs the fused form only");
+    if (c->p.t_vacuum > 0) return fail(QTRAJ_EINVAL, "qtraj_evolve_static does not run a vacuum evolution (t_vacuum > 0)");
     if (batch < 0 || batch > ST_MAX_TRAJ)
         return fail(QTRAJ_EINVAL, "batch %d outside [0, %d] (QTRAJ_STATIC_MAX_TRAJ)", batch, ST_MAX_TRAJ);
     if (n_specs <= 0 || n_specs > ST_MAX_SPECS)
@@ -941,6 +1023,7 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
     FusedInfo fi;
     auto point = [&](auto tb) {
         tb.ic = ds->ic;
+        tb.ic_cplx = 0;
         tb.ov0 = ds->ov0;
         tb.ov0_zero = ds->ov0_zero;
         tb.spec_l = ds->spec_l;

@@ -751,10 +751,18 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         const TrajDev d = a.trajs[t];
         const MediumDev md = tb.media[d.medium];
         int l = tb.spec_l[d.spec], c = tb.spec_color[d.spec];
-        const double *ic = tb.ic + (size_t)d.spec * N;
-        for (int k = g; k < N / 2; k += G) {
-            buf[k] = mk<T>((T)ic[2 * k], (T)0);
-            buf[K::odd_pos(k)] = mk<T>((T)ic[2 * k + 1], (T)0);
+        if (tb.ic_cplx) {
+            const double *ic = tb.ic + (size_t)d.spec * 2 * N;
+            for (int k = g; k < N / 2; k += G) {
+                buf[k] = mk<T>((T)ic[4 * k], (T)ic[4 * k + 1]);
+                buf[K::odd_pos(k)] = mk<T>((T)ic[4 * k + 2], (T)ic[4 * k + 3]);
+            }
+        } else {
+            const double *ic = tb.ic + (size_t)d.spec * N;
+            for (int k = g; k < N / 2; k += G) {
+                buf[k] = mk<T>((T)ic[2 * k], (T)0);
+                buf[K::odd_pos(k)] = mk<T>((T)ic[2 * k + 1], (T)0);
+            }
         }
         uint32_t kdraw = 0;
         Draws dw = draws(d.seed, 0u);

@@ -96,8 +96,13 @@ __global__ void plain_setup(Tables<double> tb, LaunchArgs a, PlainState *st, cpx
     }
     __syncthreads();
     if (s_active) {
-        const double *ic = tb.ic + (size_t)d.spec * N;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) psi[(size_t)b * N + j] = mk(ic[j], 0.0);
+        if (tb.ic_cplx) {
+            const double *ic = tb.ic + (size_t)d.spec * 2 * N;
+            for (int j = threadIdx.x; j < N; j += blockDim.x) psi[(size_t)b * N + j] = mk(ic[2 * j], ic[2 * j + 1]);
+        } else {
+            const double *ic = tb.ic + (size_t)d.spec * N;
+            for (int j = threadIdx.x; j < N; j += blockDim.x) psi[(size_t)b * N + j] = mk(ic[j], 0.0);
+        }
     }
 }
 

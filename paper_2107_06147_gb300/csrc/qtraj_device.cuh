@@ -302,7 +302,8 @@ template <typename T> struct Tables {
     const C *statV;                    // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
     const C *statV2;                   // [2][LTAB][N] the same over a full step, exp(-i (...) dt)
     const double *eig;     // [NBASIS][N] Coulomb basis, discretely normalised
-    const double *ic;      // [n_spec][N] initial states, discretely normalised
+    const double *ic;      // initial states, discretely normalised: [n_spec][N] real, or
+                           // [n_spec][N][2] (re, im) when ic_cplx (after a vacuum evolution)
     const double *ov0;     // [n_spec][NBASIS][2] initial overlaps
     const int *ov0_zero;   // [n_spec][NBASIS] structural zero of the initial overlap
     const int *spec_l;     // [n_spec]
@@ -312,6 +313,7 @@ template <typename T> struct Tables {
     double coul[2];        // coefficient of 1/r of the colour's Coulomb potential
     int max_jumps, l_cap, use_rmin;
     double r_max;
+    int ic_cplx;
 };
 
 // per-launch arguments of both forms

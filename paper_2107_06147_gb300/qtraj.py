@@ -31,7 +31,7 @@ class QtrajError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int), ("max_jumps", C.c_int),
                 ("r_max", C.c_double), ("l_cap", C.c_int), ("use_rmin", C.c_int), ("precision", C.c_int),
-                ("form", C.c_int), ("save_states", C.c_int), ("variant", C.c_int)]
+                ("form", C.c_int), ("save_states", C.c_int), ("variant", C.c_int), ("t_vacuum", C.c_double)]
 
 
 class InitSpec(C.Structure):
@@ -150,10 +150,11 @@ class Config:
     form: int = FUSED
     save_states: int = 0
     variant: int = 0
+    t_vacuum: float = 0.0
 
     def params(self) -> Params:
         return Params(self.alpha_s, self.Nc, self.deriv_type, self.max_jumps, self.r_max, self.l_cap, self.use_rmin,
-                      self.precision, self.form, self.save_states, self.variant)
+                      self.precision, self.form, self.save_states, self.variant, self.t_vacuum)
 
 
 def init_spec(kind="gauss", width=0.2, n=1, l=0, color=0) -> InitSpec:

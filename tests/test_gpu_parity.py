@@ -224,6 +224,47 @@ def test_kappa_lattice_fits(q, form, precision):
         check_fp32(q, obs, ref, u, uref)
 
 
+@pytest.mark.parametrize("form,precision", [(0, 0), (1, 0), (0, 1)])
+def test_vacuum_evolution(q, form, precision):
+    """Vacuum evolution of every initial state before the medium (t_vacuum = 0.3 GeV^-1, 300 steps at
+    T = 0; Sec. 3.5 item 3), singlet and octet, Gaussian and Coulomb states: the trajectories and the
+    survival ratios (referred to the evolved state) against the oracle."""
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=64, n_traj=24, seed=33)
+    g, inits, media = oracle_inputs(w)
+    g.t_vac = 0.3
+    import oracle as o
+    ref, _, uref = o.run_batch(g, inits, w.init_idx, media, w.medium_idx, w.seeds, want_states=True)
+    obs, u = run_gpu(q, w, precision, form=form, t_vacuum=0.3)
+    if precision == 0:
+        check_fp64(q, obs, ref, u, uref)
+    else:
+        check_fp32(q, obs, ref, u, uref)
+    # the reference of the ratios is the evolved state: a Coulomb 1S in a medium without kappa and
+    # gamma keeps S(1S) = 1 up to the discretisation's leakage
+    w1 = inputs.small_parity(N=256, n_traj=2, seed=34)
+    w1.grid.L = 10.0
+    w1.inits = [inputs.InitSpec("coulomb", 0.0, 1, 0, 0)]
+    w1.init_idx[:] = 0
+    w1.media = [inputs.MediumSpec(0.4, 0.6, 0.38, 0.0, 0.0)]
+    w1.medium_idx[:] = 0
+    o1, _ = run_gpu(q, w1, precision, form=form, t_vacuum=0.3)
+    assert np.abs(o1["surv"][:, 0] - 1).max() < 1e-5
+
+
+def test_static_entry_rejects_vacuum_evolution(q):
+    import ctypes as C
+    import torch
+    e = q.Engine(q.Config(N=64, L=2.5, dt=0.001, t_vacuum=0.1))
+    out = torch.zeros(q.OBS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    sp = (q.InitSpec * 1)(q.init_spec())
+    md = (q.Medium * 1)(q.medium())
+    sd = (C.c_uint64 * 1)(0)
+    st = e.lib.qtraj_evolve_static(e.ctx, 1, sp, 1, None, md, 1, None, sd, C.c_void_p(out.data_ptr()), None)
+    assert st == 1 and b"vacuum" in e.lib.qtraj_last_error(e.ctx)
+    e.close()
+
+
 @pytest.mark.parametrize("N", [64, 1024])
 def test_fp32_no_jump_norm_has_no_drift(q, N):
     """FP32 against FP64 on the no-jump runs (each a whole medium of 1,500-3,000 steps without a jump):
