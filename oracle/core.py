@@ -47,7 +47,8 @@ class Init(C.Structure):
 
 class Medium(C.Structure):
     _fields_ = [("T0", C.c_double), ("tau0", C.c_double), ("Tf", C.c_double),
-                ("kappa_hat", C.c_double), ("gamma_hat", C.c_double)]
+                ("kappa_hat", C.c_double), ("gamma_hat", C.c_double), ("kind", C.c_int),
+                ("tab_tau", C.POINTER(C.c_double)), ("tab_T", C.POINTER(C.c_double)), ("tab_n", C.c_int)]
 
 
 class Obs(C.Structure):
@@ -147,7 +148,17 @@ def init_spec(kind: str = "gauss", width: float = 0.2, n: int = 1, l: int = 0, c
 
 
 def medium(T0=0.425, tau0=0.6, Tf=0.25, kappa_hat=5.0, gamma_hat=0.0) -> Medium:
-    return Medium(T0, tau0, Tf, kappa_hat, gamma_hat)
+    return Medium(T0, tau0, Tf, kappa_hat, gamma_hat, 0, None, None, 0)
+
+
+def table_medium(tau, T, Tf=0.25, kappa_hat=5.0, gamma_hat=0.0) -> Medium:
+    """A tabulated T(tau) medium (tau ascending, fm/c; T in GeV).  The record points into its own
+    copies of the arrays, kept alive on the record."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    m = Medium(float(T[0]), float(tau[0]), Tf, kappa_hat, gamma_hat, 1, _dp(tau), _dp(T), len(tau))
+    m._keep = (tau, T)
+    return m
 
 
 # ------------------------------------------------------------------------------------------------

@@ -64,7 +64,15 @@ typedef struct {
 } oqt_params;
 
 typedef struct { int kind; double width; int n, l, color; } oqt_init;  /* kind 0 Gaussian, 1 Coulomb */
-typedef struct { double T0, tau0, Tf, kappa_hat, gamma_hat; } oqt_medium;
+/* kind 0: Bjorken T0 (tau0/tau)^{1/3} from tau0; kind 1: T(tau) interpolated linearly in the table
+ * (tab_tau[i], tab_T[i]), i < tab_n, tau ascending (fm/c), from tab_tau[0] (Table 1
+ * temperatureEvolution 1/2; the file formats of App. B).  Both end once T < Tf. */
+typedef struct {
+    double T0, tau0, Tf, kappa_hat, gamma_hat;
+    int kind;
+    const double *tab_tau, *tab_T;
+    int tab_n;
+} oqt_medium;
 
 typedef struct {
     double surv[OQT_NBASIS];
@@ -162,20 +170,51 @@ static double oqt_CF(double Nc) { return (Nc * Nc - 1.0) / (2.0 * Nc); }
 /* Bohr radius a0 = 1/(mu alpha), mu = M/2 the reduced mass, alpha = C_F alpha_s */
 double oqt_bohr_radius(const oqt_params *p) { return 2.0 / (p->M * oqt_CF(p->Nc) * p->alpha_s); }
 
-/* number of steps until T(tau) falls below Tf */
+/* a tabulated temperature at tau: linear between the two neighbouring points; before the first
+ * point the first temperature, after the last the last */
+static double oqt_table_T(const oqt_medium *m, double tau)
+{
+    if (tau <= m->tab_tau[0]) return m->tab_T[0];
+    for (int i = 0; i + 1 < m->tab_n; i++)
+        if (tau < m->tab_tau[i + 1])
+            return m->tab_T[i] + (m->tab_T[i + 1] - m->tab_T[i]) * (tau - m->tab_tau[i]) /
+                                     (m->tab_tau[i + 1] - m->tab_tau[i]);
+    return m->tab_T[m->tab_n - 1];
+}
+
+/* the proper time the medium starts at */
+static double oqt_tau_start(const oqt_medium *m) { return m->kind == 1 ? m->tab_tau[0] : m->tau0; }
+
+/* number of steps until T(tau) falls below Tf: ceil((tau_f - tau_start) / (hbar c dt)), with tau_f
+ * from T0 (tau0/tau_f)^{1/3} = Tf (Bjorken) or the first crossing of Tf by the table (its last tau if
+ * it never falls below Tf) */
 int oqt_n_steps(const oqt_params *p, const oqt_medium *m)
 {
-    double tau_f = m->tau0 * pow(m->T0 / m->Tf, 3.0);
-    double steps = ceil((tau_f - m->tau0) / (OQT_HBARC * p->dt));
+    double tau_f;
+    if (m->kind == 1) {
+        tau_f = m->tab_tau[m->tab_n - 1];
+        if (m->tab_T[0] < m->Tf) tau_f = m->tab_tau[0];
+        else
+            for (int i = 0; i + 1 < m->tab_n; i++)
+                if (m->tab_T[i + 1] < m->Tf) {
+                    tau_f = m->tab_tau[i] + (m->tab_tau[i + 1] - m->tab_tau[i]) * (m->tab_T[i] - m->Tf) /
+                                                (m->tab_T[i] - m->tab_T[i + 1]);
+                    break;
+                }
+    } else {
+        tau_f = m->tau0 * pow(m->T0 / m->Tf, 3.0);
+    }
+    double steps = ceil((tau_f - oqt_tau_start(m)) / (OQT_HBARC * p->dt));
     if (steps < 0) steps = 0;
     return (int)steps;
 }
 
-/* T(tau_n)^3 for step n: T0^3 tau0 / tau_n with tau_n = tau0 + n dt hbar c */
+/* T(tau_n)^3 for step n, tau_n = tau_start + n dt hbar c: T0^3 tau0 / tau_n (Bjorken) or the
+ * table's temperature cubed */
 double oqt_T3(const oqt_params *p, const oqt_medium *m, int n)
 {
-    double tau = m->tau0 + (double)n * p->dt * OQT_HBARC;
-    double T = m->T0 * pow(m->tau0 / tau, 1.0 / 3.0);
+    double tau = oqt_tau_start(m) + (double)n * p->dt * OQT_HBARC;
+    double T = m->kind == 1 ? oqt_table_T(m, tau) : m->T0 * pow(m->tau0 / tau, 1.0 / 3.0);
     return T * T * T;
 }
 

@@ -313,6 +313,46 @@ def test_kappa_fit_medium_decays_with_kappa_of_T(oracle_lib, which):
     assert abs(rates[1] / (gams[1] * k[0] / k[1]) - 1) > 0.15            # ... and the early value is wrong late
 
 
+def test_table_profile_linear_pieces_and_end(oracle_lib):
+    """Tabulated T(tau) (Table 1 temperatureEvolution 1/2; App. B formats): step n uses T linearly
+    interpolated at tau_n = tau_1 + n dt hbar c; the evolution ends at the first crossing of Tf
+    (ceil of the steps to it), at the table's last tau if T never falls below Tf, and at once if it
+    starts below Tf."""
+    o = oracle_lib
+    g = o.Grid(N=64, L=2.0, dt=0.001)
+    hc = 0.1973269804
+    tau, T = np.array([0.6, 1.0, 2.0]), np.array([0.5, 0.4, 0.2])
+    m = o.table_medium(tau, T, Tf=0.3)
+    assert o.n_steps(g, m) == int(np.ceil((1.5 - 0.6) / (hc * g.dt)))      # crossing at tau = 1.5
+    for n in (0, 700, 2027, 2028, 4000):
+        t = 0.6 + n * g.dt * hc
+        Tex = 0.5 - 0.25 * (t - 0.6) if t < 1.0 else 0.4 - 0.2 * (t - 1.0)
+        assert abs(o.T3(g, m, n) - Tex ** 3) < 1e-14
+    assert o.n_steps(g, o.table_medium(tau, T, Tf=0.1)) == int(np.ceil((2.0 - 0.6) / (hc * g.dt)))
+    assert abs(o.T3(g, o.table_medium(tau, T, Tf=0.1), 10 ** 5) - 0.2 ** 3) < 1e-15   # held after the end
+    assert o.n_steps(g, o.table_medium(tau, T, Tf=0.6)) == 0
+
+
+def test_table_sampled_from_bjorken_converges(oracle_lib):
+    """A table sampled from a Bjorken profile reproduces the Bjorken evolution: after 5000 steps the
+    no-jump norm differs by O(dtau^2) of the sampling (the difference falls ~4x when dtau halves)."""
+    o = oracle_lib
+    g = o.Grid(N=128, L=5.0, dt=0.001)
+    u0 = o.initial_state(g, o.init_spec("gauss", 0.3, 1, 0, 0))
+    bj = o.medium(T0=0.45, tau0=0.6, Tf=0.3, kappa_hat=5.0, gamma_hat=-1.0)
+    _, href = o.evolve_nojump(g, u0, 0, 0, bj, 0, 5000)
+    errs = []
+    for d in (0.04, 0.02):
+        tau = np.arange(0.6, 2.6, d)
+        T = 0.45 * (0.6 / tau) ** (1.0 / 3.0)
+        tm = o.table_medium(tau, T, Tf=0.3, kappa_hat=5.0, gamma_hat=-1.0)
+        _, h = o.evolve_nojump(g, u0, 0, 0, tm, 0, 5000)
+        errs.append(abs(h[-1] - href[-1]) / href[-1])
+        # the interpolated profile lies above the convex Bjorken one, so it crosses Tf a little later
+        assert 0 <= o.n_steps(g, tm) - o.n_steps(g, bj) <= 4
+    assert errs[0] < 3e-4 and 3.0 < errs[0] / errs[1] < 5.0
+
+
 # ------------------------------------------------------------------------------------------------
 # trajectories: waiting-time statistics, shortcut exactness, options
 # ------------------------------------------------------------------------------------------------
