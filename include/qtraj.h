@@ -83,7 +83,13 @@ typedef struct {
 } qtraj_init_spec;
 
 /* Medium seen by a trajectory.  kind 0 = Bjorken T(tau) = T0 (tau0/tau)^{1/3} from tau0 until
- * T < Tf (Sec. 3.4, Table 1); gamma_hat <= 0 and kappa_hat are the transport coefficients
+ * T < Tf (Sec. 3.4, Table 1).  kind 1 = tabulated T(tau) (Table 1 temperatureEvolution 1/2, the
+ * file formats of App. B): the points [table_offset, table_offset + table_len) of the context's
+ * profile store (qtraj_set_profiles), tau strictly ascending; the medium starts at the first tau,
+ * step n uses T linearly interpolated at tau_n = tau_1 + n dt hbar c (the last T past the last
+ * point), and it ends after ceil((tau_f - tau_1) / (hbar c dt)) steps, tau_f the first crossing of
+ * Tf by the interpolated T (the last tau if T stays >= Tf); T0 and tau0 are ignored.  gamma_hat <= 0
+ * and kappa_hat are the transport coefficients
  * kappa = kappa_hat T^3, gamma = gamma_hat T^3 of the potential (App. E).  kappa_hat >= 0 is a
  * constant; kappa_hat = -1, -2, -3 selects the central, lower or upper lattice fit
  * kappa_hat(T) = 1 / (a x^{3/2} + b x + c x^{1/2} + d), x = T / T_c, T_c = 0.155 GeV (App. E, the
@@ -92,6 +98,7 @@ typedef struct {
     int kind;
     double T0, tau0, Tf;
     double kappa_hat, gamma_hat;
+    int table_offset, table_len; /* kind 1 only */
 } qtraj_medium;
 
 #define QTRAJ_NBASIS 6 /* 1S, 2S, 1P, 3S, 2P, 1D = Coulomb (n,l) (1,0) (2,0) (2,1) (3,0) (3,1) (3,2) */
@@ -143,6 +150,12 @@ qtraj_status qtraj_init(qtraj_ctx *ctx, void *d_workspace, size_t bytes, int n_t
  * scheduler reuse one bound workspace for batches of different composition.  EINVAL if n exceeds the
  * bound n_traj or an index is out of range. */
 qtraj_status qtraj_set_spec_idx(qtraj_ctx *ctx, const int *spec_idx, int n);
+
+/* Sets the context's profile store: n_points (tau [fm/c], T [GeV]) points from host arrays,
+ * referred to by kind-1 media through (table_offset, table_len).  Several profiles share the store
+ * back to back.  Waits for the context's queued work, then uploads (synchronous); replaces the
+ * previous store.  EINVAL for n_points < 2 or a non-finite or negative value. */
+qtraj_status qtraj_set_profiles(qtraj_ctx *ctx, const double *tau, const double *T, int n_points);
 
 /* Evolves trajectories [0, batch) of the bound workspace through their media: trajectory t sees
  * media[medium_idx[t]] (same NULL rule as qtraj_init) and draws its waiting-time thresholds and

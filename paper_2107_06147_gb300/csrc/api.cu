@@ -103,6 +103,8 @@ struct qtraj_ctx {
     double *ic = nullptr, *ov0 = nullptr;
     int *ov0_zero = nullptr, *spec_l = nullptr, *spec_color = nullptr;
     bool ic_cplx = false;   // ic holds complex states (after a vacuum evolution)
+    double *prof = nullptr; // profile store of tabulated media: (tau, T) pairs
+    std::vector<double> prof_host;
     int n_spec = 0;
     std::vector<qtraj_init_spec> specs;
     std::vector<int> spec_idx;
@@ -231,6 +233,7 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     t.use_rmin = c->p.use_rmin;
     t.r_max = c->p.r_max;
     t.ic_cplx = c->ic_cplx ? 1 : 0;
+    t.prof = c->prof;
     return t;
 }
 
@@ -245,10 +248,30 @@ template <typename P> void free_typed(P *&p)
     p = nullptr;
 }
 
-int medium_steps(double dt, const qtraj_medium &m)
+// steps until T falls below Tf: ceil((tau_f - tau_start) / (hbar c dt)) with tau_f where the Bjorken
+// T0 (tau0/tau)^{1/3}, or the table's interpolated T, first crosses Tf (a table that stays >= Tf ends
+// at its last tau, one that starts below Tf at once)
+int medium_steps(double dt, const qtraj_medium &m, const double *prof)
 {
-    const double tau_f = m.tau0 * std::pow(m.T0 / m.Tf, 3.0);
-    double s = std::ceil((tau_f - m.tau0) / (HBARC * dt));
+    double tau_s = m.tau0, tau_f;
+    if (m.kind == 1) {
+        const double *p = prof + 2 * (size_t)m.table_offset;
+        const int n = m.table_len;
+        tau_s = p[0];
+        tau_f = p[2 * (n - 1)];
+        if (p[1] < m.Tf) {
+            tau_f = tau_s;
+        } else {
+            for (int i = 0; i + 1 < n; ++i)
+                if (p[2 * i + 3] < m.Tf) {
+                    tau_f = p[2 * i] + (p[2 * i + 2] - p[2 * i]) * (p[2 * i + 1] - m.Tf) / (p[2 * i + 1] - p[2 * i + 3]);
+                    break;
+                }
+        }
+    } else {
+        tau_f = m.tau0 * std::pow(m.T0 / m.Tf, 3.0);
+    }
+    double s = std::ceil((tau_f - tau_s) / (HBARC * dt));
     if (s < 0) s = 0;
     return (int)s;
 }
@@ -260,10 +283,24 @@ int kappa_fit_index(double k)
     return k == -1.0 ? 1 : k == -2.0 ? 2 : k == -3.0 ? 3 : 0;
 }
 
-const char *medium_check(const qtraj_medium &q)
+// prof: the (tau, T) pairs of the context's profile store (n_prof points), or nullptr where
+// tabulated media are not available
+const char *medium_check(const qtraj_medium &q, const double *prof = nullptr, int n_prof = 0)
 {
-    if (q.kind != 0) return "only kind 0 (Bjorken) is supported";
-    if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) return "T0, tau0, Tf must be positive";
+    if (q.kind == 1) {
+        if (!prof) return "tabulated media (kind 1) need a context with a profile store (qtraj_set_profiles)";
+        if (q.table_offset < 0 || q.table_len < 2 || q.table_offset > n_prof - q.table_len)
+            return "table_offset/table_len outside the profile store (at least 2 points)";
+        const double *p = prof + 2 * (size_t)q.table_offset;
+        for (int i = 0; i + 1 < q.table_len; ++i)
+            if (!(p[2 * i + 2] > p[2 * i])) return "the table's tau must be strictly ascending";
+        if (!(p[0] > 0)) return "the table's tau must be positive";
+        if (!(q.Tf > 0)) return "Tf must be positive";
+    } else if (q.kind != 0) {
+        return "kind must be 0 (Bjorken) or 1 (tabulated)";
+    } else if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) {
+        return "T0, tau0, Tf must be positive";
+    }
     if (!(q.gamma_hat <= 0)) return "gamma_hat <= 0 required";
     if (kappa_fit_index(q.kappa_hat) != 0) {
         if (!(q.Tf >= 0.155)) return "a kappa_hat lattice fit needs Tf >= T_c = 0.155 GeV";
@@ -278,8 +315,15 @@ MediumDev encode_medium(const qtraj_ctx *c, const qtraj_medium &q)
 {
     MediumDev d{};
     const double Nc = c->p.Nc;
-    d.A = q.T0 * q.T0 * q.T0 * q.tau0;
-    d.tau0 = q.tau0;
+    d.kind = q.kind;
+    if (q.kind == 1) {
+        d.tab_off = q.table_offset;
+        d.tab_len = q.table_len;
+        d.tau0 = c->prof_host[2 * (size_t)q.table_offset];
+    } else {
+        d.A = q.T0 * q.T0 * q.T0 * q.tau0;
+        d.tau0 = q.tau0;
+    }
     d.dtau = c->dt * HBARC;
     d.kfit = kappa_fit_index(q.kappa_hat);
     const double kap = d.kfit ? 1.0 : q.kappa_hat;
@@ -442,6 +486,7 @@ void qtraj_destroy(qtraj_ctx *c)
     free_typed(c->ov0_zero);
     free_typed(c->spec_l);
     free_typed(c->spec_color);
+    free_typed(c->prof);
     free_typed(c->media);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->ev_stage) cudaEventDestroy(c->ev_stage);
@@ -539,6 +584,26 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
     return QTRAJ_OK;
 }
 
+qtraj_status qtraj_set_profiles(qtraj_ctx *c, const double *tau, const double *T, int n_points)
+{
+    g_err.clear();
+    if (!c || !tau || !T) return fail(QTRAJ_EINVAL, "null argument");
+    if (n_points < 2) return fail(QTRAJ_EINVAL, "n_points must be at least 2");
+    std::vector<double> h(2 * (size_t)n_points);
+    for (int i = 0; i < n_points; ++i) {
+        if (!std::isfinite(tau[i]) || !std::isfinite(T[i]) || tau[i] < 0 || T[i] < 0)
+            return fail(QTRAJ_EINVAL, "point %d: tau and T must be finite and >= 0", i);
+        h[2 * (size_t)i] = tau[i];
+        h[2 * (size_t)i + 1] = T[i];
+    }
+    CK(cudaDeviceSynchronize());
+    free_typed(c->prof);
+    CK(cudaMalloc(&c->prof, sizeof(double) * h.size()));
+    CK(cudaMemcpy(c->prof, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+    c->prof_host = std::move(h);
+    return QTRAJ_OK;
+}
+
 qtraj_status qtraj_set_spec_idx(qtraj_ctx *c, const int *spec_idx, int n)
 {
     g_err.clear();
@@ -568,8 +633,10 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
     std::vector<int> steps(n_media);
     for (int m = 0; m < n_media; ++m) {
         const qtraj_medium &q = media[m];
-        if (const char *why = medium_check(q)) return fail(QTRAJ_EINVAL, "medium %d: %s", m, why);
-        steps[m] = medium_steps(c->dt, q);
+        if (const char *why = medium_check(q, c->prof_host.empty() ? nullptr : c->prof_host.data(),
+                                           (int)(c->prof_host.size() / 2)))
+            return fail(QTRAJ_EINVAL, "medium %d: %s", m, why);
+        steps[m] = medium_steps(c->dt, q, c->prof_host.data());
         md[m] = encode_medium(c, q);
     }
     std::vector<TrajDev> tr(batch);
@@ -982,7 +1049,7 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
     for (int m = 0; m < n_media; ++m) {
         const qtraj_medium &q = media[m];
         if (const char *why = medium_check(q)) return fail(QTRAJ_EINVAL, "medium %d: %s", m, why);
-        steps[m] = medium_steps(c->dt, q);
+        steps[m] = medium_steps(c->dt, q, nullptr);
         h.media[m] = encode_medium(c, q);
     }
     for (int i = 0; i < n_specs * n_media; ++i) g_static_pair_group[i] = -1;

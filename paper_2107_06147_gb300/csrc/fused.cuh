@@ -772,7 +772,13 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         const int ns = d.n_steps;
         // per-step scalars in the working precision: T^3 = A / (tau0 + n dtau)
         const T mA = (T)md.A, mtau0 = (T)md.tau0, mdtau = (T)md.dtau;
-        T T3b = mA / mtau0;
+        const double *prof = md.kind == 1 ? tb.prof + 2 * (size_t)md.tab_off : nullptr;
+        int seg = 0;
+        // T(tau_n)^3: Bjorken, or the table at tau_n = tau_1 + n dtau
+        auto T3_of = [&](int n) -> T {
+            return prof ? table_T3<T>(prof, md.tab_len, mtau0 + (T)n * mdtau, seg) : mA / (mtau0 + (T)n * mdtau);
+        };
+        T T3b = T3_of(0);
         T K3b = kappa_T3<T>(md.kfit, T3b);   // kappa_hat(T) T^3 when kappa_hat follows a lattice fit
         if (ns > 0) {
             __syncthreads();
@@ -782,7 +788,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         for (int n = 0; n < ns; ++n) {
             const T T3a = T3b, K3a = K3b;
             const bool last = (n + 1 == ns);
-            T3b = mA / (mtau0 + (T)(n + 1) * mdtau);
+            T3b = T3_of(n + 1);
             K3b = kappa_T3<T>(md.kfit, T3b);
             __syncthreads();
 #pragma unroll 1

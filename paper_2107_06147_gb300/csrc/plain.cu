@@ -13,7 +13,12 @@ namespace {
 
 constexpr int PB = 256; // threads of the per-trajectory kernels
 
-__device__ __forceinline__ double T3_of(const MediumDev &m, int n) { return m.A / (m.tau0 + (double)n * m.dtau); }
+__device__ __forceinline__ double T3_of(const Tables<double> &tb, const MediumDev &m, int n)
+{
+    const double tau = m.tau0 + (double)n * m.dtau;
+    if (m.kind == 1) return table_T3_at(tb.prof + 2 * (size_t)m.tab_off, m.tab_len, tau);
+    return m.A / tau;
+}
 
 // K3 = kappa_T3(md.kfit, T3): the T^3 of the real exponent, times kappa_hat(T) for a fitted medium
 __device__ __forceinline__ cpx<double> space_factor(const Tables<double> &tb, int N, const MediumDev &md, int c, int l,
@@ -118,7 +123,7 @@ __global__ void plain_space_pre(Tables<double> tb, LaunchArgs a, const PlainStat
     const PlainState s = st[b];
     if (!running(s, d, n)) return;
     const MediumDev md = tb.media[d.medium];
-    const double T3 = T3_of(md, n), K3 = kappa_T3<double>(md.kfit, T3);
+    const double T3 = T3_of(tb, md, n), K3 = kappa_T3<double>(md.kfit, T3);
     const cpx<double> *p = psi + (size_t)b * N;
     cpx<double> *o = y + (size_t)b * N;
     if (q == 0) {
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(PB) plain_post(Tables<double> tb, LaunchArgs a
         }
     } else {
         const MediumDev md = tb.media[d.medium];
-        const double T3 = T3_of(md, n), K3 = kappa_T3<double>(md.kfit, T3);
+        const double T3 = T3_of(tb, md, n), K3 = kappa_T3<double>(md.kfit, T3);
         double acc = 0.0;
         for (int j = threadIdx.x; j < N; j += PB) {
             const cpx<double> f = space_factor(tb, N, md, s.c, s.l, j, T3, K3) * Sb[j];

@@ -260,8 +260,8 @@ template <typename T> struct DFT<T, 16> {
 // device records
 // ------------------------------------------------------------------------------------------------
 struct MediumDev {
-    double A;       // T0^3 tau0, so T(tau_n)^3 = A / (tau0 + n dtau)
-    double tau0;    // fm/c
+    double A;       // T0^3 tau0, so T(tau_n)^3 = A / (tau0 + n dtau)  (kind 0)
+    double tau0;    // fm/c: tau of step 0 (kind 1: the table's first tau)
     double dtau;    // dt * hbar c, fm/c per step
     double er[2];   // -kappa_c dt/2 per colour: the real exponent of the space kernel is er*T^3*r^2
     double ei[2];   // -gamma_c dt/2 per colour: the phase of the space kernel is ei*T^3*r^2
@@ -269,7 +269,35 @@ struct MediumDev {
     double eij[2];  // ei * dr^2 / pi: the phase is pi * eij * T^3 * j^2
     int kfit;       // 0: constant kappa_hat, folded into er/erj; 1, 2, 3: er/erj are per unit kappa_hat
                     // and T^3 in the real exponent becomes kappa_hat(T) T^3 from lattice fit kfit
+    int kind;       // 0 Bjorken; 1 tabulated: points [tab_off, tab_off + tab_len) of the profile store
+    int tab_off, tab_len;
 };
+
+// T^3 at tau of a tabulated medium, p = its (tau, T) pairs: linear in T between the neighbouring
+// points, the first/last T outside.  seg is the caller's segment index (p[seg].tau <= tau), moved
+// forward only, so a trajectory walks its table once.
+template <typename T> __device__ __forceinline__ T table_T3(const double *p, int len, T tau, int &seg)
+{
+    while (seg + 2 < len && tau >= (T)p[2 * (seg + 1)]) ++seg;
+    const T t0 = (T)p[2 * seg], t1 = (T)p[2 * seg + 2], T0 = (T)p[2 * seg + 1], T1 = (T)p[2 * seg + 3];
+    T f = (tau - t0) / (t1 - t0);
+    f = f < (T)0 ? (T)0 : (f > (T)1 ? (T)1 : f);
+    const T Tt = T0 + f * (T1 - T0);
+    return Tt * Tt * Tt;
+}
+
+// the same from scratch (binary search), for kernels that do not carry a segment index
+__device__ __forceinline__ double table_T3_at(const double *p, int len, double tau)
+{
+    int lo = 0, hi = len - 1;   // find the last point with tau_i <= tau, at most len - 2
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p[2 * mid] <= tau) lo = mid;
+        else hi = mid;
+    }
+    int seg = lo;
+    return table_T3<double>(p, len, tau, seg);
+}
 
 // kappa_hat(T) T^3 given T^3: kfit 0 returns T^3 (kappa_hat is folded into the exponent's
 // coefficient); kfit 1, 2, 3 multiply by the central, lower or upper lattice fit of the Munich
@@ -314,6 +342,7 @@ template <typename T> struct Tables {
     int max_jumps, l_cap, use_rmin;
     double r_max;
     int ic_cplx;
+    const double *prof;    // profile store: (tau, T) pairs of the tabulated media
 };
 
 // per-launch arguments of both forms

@@ -40,7 +40,8 @@ class InitSpec(C.Structure):
 
 class Medium(C.Structure):
     _fields_ = [("kind", C.c_int), ("T0", C.c_double), ("tau0", C.c_double), ("Tf", C.c_double),
-                ("kappa_hat", C.c_double), ("gamma_hat", C.c_double)]
+                ("kappa_hat", C.c_double), ("gamma_hat", C.c_double), ("table_offset", C.c_int),
+                ("table_len", C.c_int)]
 
 
 class RunStats(C.Structure):
@@ -67,8 +68,8 @@ class ServerConfig(C.Structure):
 # qtraj_traj_desc as a numpy record, to build large requests without a Python loop
 TRAJ_DESC_DTYPE = np.dtype([("N", "<i4"), ("spec", "<i4"), ("kind", "<i4"), ("_pad", "<i4"), ("T0", "<f8"),
                             ("tau0", "<f8"), ("Tf", "<f8"), ("kappa_hat", "<f8"), ("gamma_hat", "<f8"),
-                            ("seed", "<u8")])
-assert TRAJ_DESC_DTYPE.itemsize == C.sizeof(TrajDesc) == 64
+                            ("table_offset", "<i4"), ("table_len", "<i4"), ("seed", "<u8")])
+assert TRAJ_DESC_DTYPE.itemsize == C.sizeof(TrajDesc) == 72
 
 OBS_DTYPE = np.dtype([("surv", "<f8", NBASIS), ("ov_re", "<f8", NBASIS), ("ov_im", "<f8", NBASIS),
                       ("norm2", "<f8"), ("r0", "<f8"), ("l", "<i4"), ("color", "<i4"), ("n_jumps", "<i4"),
@@ -84,6 +85,7 @@ _PROTOS = {
     "qtraj_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.POINTER(InitSpec), C.c_int,
                              C.POINTER(C.c_int)]),
     "qtraj_set_spec_idx": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int]),
+    "qtraj_set_profiles": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
     "qtraj_evolve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Medium), C.c_int, C.POINTER(C.c_int),
                                C.POINTER(C.c_uint64), C.c_void_p]),
     "qtraj_observables": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -162,7 +164,13 @@ def init_spec(kind="gauss", width=0.2, n=1, l=0, color=0) -> InitSpec:
 
 
 def medium(T0=0.425, tau0=0.6, Tf=0.25, kappa_hat=5.0, gamma_hat=0.0) -> Medium:
-    return Medium(0, T0, tau0, Tf, kappa_hat, gamma_hat)
+    return Medium(0, T0, tau0, Tf, kappa_hat, gamma_hat, 0, 0)
+
+
+def table_medium(table_offset: int, table_len: int, Tf=0.25, kappa_hat=5.0, gamma_hat=0.0) -> Medium:
+    """A tabulated T(tau) medium: points [table_offset, table_offset + table_len) of the context's
+    profile store (Engine.set_profiles)."""
+    return Medium(1, 0.0, 0.0, Tf, kappa_hat, gamma_hat, table_offset, table_len)
 
 
 class Engine:
@@ -211,6 +219,13 @@ class Engine:
             idx = self._spec_idx.ctypes.data_as(C.POINTER(C.c_int))
         _check(self.lib.qtraj_init(self.ctx, C.c_void_p(ptr), have, n_traj, arr, len(specs), idx), self.ctx)
         self.n_traj = n_traj
+
+    def set_profiles(self, tau, T):
+        """Sets the profile store of tabulated media: points (tau [fm/c], T [GeV]); synchronous."""
+        t = np.ascontiguousarray(tau, dtype=np.float64)
+        v = np.ascontiguousarray(T, dtype=np.float64)
+        dp = C.POINTER(C.c_double)
+        _check(self.lib.qtraj_set_profiles(self.ctx, t.ctypes.data_as(dp), v.ctypes.data_as(dp), len(t)), self.ctx)
 
     def set_spec_idx(self, spec_idx):
         """Re-binds the initial state of trajectories [0, len(spec_idx)) (host-side, no device sync)."""

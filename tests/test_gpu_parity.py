@@ -252,6 +252,70 @@ def test_vacuum_evolution(q, form, precision):
     assert np.abs(o1["surv"][:, 0] - 1).max() < 1e-5
 
 
+def _profiles():
+    """Three tabulated T(tau) profiles: a Bjorken one sampled every 0.05 fm/c, a hydro-like one that
+    rises and then falls, and one that ends above Tf (the evolution stops at its last tau)."""
+    t1 = np.arange(0.6, 1.6, 0.05)
+    p1 = (t1, 0.5 * (0.6 / t1) ** (1.0 / 3.0))
+    t2 = np.array([0.3, 0.5, 0.7, 1.0, 1.4, 2.0])
+    p2 = (t2, np.array([0.42, 0.47, 0.5, 0.46, 0.41, 0.33]))
+    t3 = np.array([0.8, 1.0, 1.3])
+    p3 = (t3, np.array([0.45, 0.44, 0.43]))
+    return [p1, p2, p3]
+
+
+@pytest.mark.parametrize("form,precision", [(0, 0), (1, 0), (0, 1)])
+def test_tabulated_profiles(q, form, precision):
+    """Media with tabulated T(tau) (kind 1; linear interpolation, end at the first crossing of Tf or
+    the table's end) beside a Bjorken one, against the oracle on the same tables."""
+    import torch
+    import oracle as o
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=64, n_traj=36, seed=41)
+    g, inits, _ = oracle_inputs(w)
+    g.use_rmin = 0                                     # every trajectory walks its table
+    prof = _profiles()
+    kg = [(5.0, -1.0), (3.5, 0.0), (-1.0, -2.0)]      # the last uses the central kappa_hat(T) fit
+    om = [o.table_medium(t, T, Tf=0.4, kappa_hat=k, gamma_hat=gg) for (t, T), (k, gg) in zip(prof, kg)]
+    om.append(o.medium(0.5, 0.6, 0.42, 4.0, -1.0))
+    mi = (np.arange(36) % 4).astype(np.int32)
+    ref, _, uref = o.run_batch(g, inits, w.init_idx, om, mi, w.seeds, want_states=True)
+    assert (ref["n_steps_exec"] > 0).all() and (ref["n_jumps"] > 0).sum() >= 3
+    e = q.Engine(q.Config(N=64, L=w.grid.L, dt=w.grid.dt, precision=precision, form=form, save_states=1,
+                          use_rmin=0))
+    e.set_profiles(np.concatenate([p[0] for p in prof]), np.concatenate([p[1] for p in prof]))
+    off = np.cumsum([0] + [len(p[0]) for p in prof])
+    gm = [q.table_medium(int(off[i]), len(prof[i][0]), 0.4, kg[i][0], kg[i][1]) for i in range(3)]
+    gm.append(q.medium(0.5, 0.6, 0.42, 4.0, -1.0))
+    e.init([q.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits], 36, w.init_idx)
+    e.evolve(gm, w.seeds, mi)
+    obs = e.observables()
+    u = e.states()
+    torch.cuda.synchronize()
+    e.close()
+    if precision == 0:
+        check_fp64(q, obs, ref, u, uref)
+    else:
+        check_fp32(q, obs, ref, u, uref)
+
+
+def test_tabulated_profile_errors(q):
+    e = q.Engine(q.Config(N=64, L=2.5, dt=0.001))
+    e.init([q.init_spec()], 2)
+    with pytest.raises(q.QtrajError):
+        e.evolve([q.table_medium(0, 3, 0.3)], np.arange(2, dtype=np.uint64))         # no store yet
+    e.set_profiles([0.6, 1.0, 0.9, 2.0], [0.5, 0.4, 0.35, 0.3])
+    with pytest.raises(q.QtrajError):
+        e.evolve([q.table_medium(0, 4, 0.3)], np.arange(2, dtype=np.uint64))         # tau not ascending
+    with pytest.raises(q.QtrajError):
+        e.evolve([q.table_medium(3, 2, 0.3)], np.arange(2, dtype=np.uint64))         # outside the store
+    with pytest.raises(q.QtrajError):
+        e.set_profiles([0.6], [0.5])                                                  # one point
+    e.evolve([q.table_medium(0, 2, 0.3)], np.arange(2, dtype=np.uint64))
+    e.observables()
+    e.close()
+
+
 def test_static_entry_rejects_vacuum_evolution(q):
     import ctypes as C
     import torch
