@@ -58,6 +58,9 @@ class Obs(C.Structure):
                 ("flags", C.c_int), ("first_jump_step", C.c_int)]
 
 
+TRACE_DTYPE = np.dtype([("step", "<i4"), ("color", "<i4"), ("l", "<i4"), ("flags", "<i4"), ("norm2", "<f8"),
+                        ("ov2", "<f8", NBASIS), ("r_ratio", "<f8")])
+
 OBS_DTYPE = np.dtype([("surv", "<f8", NBASIS), ("ov_re", "<f8", NBASIS), ("ov_im", "<f8", NBASIS),
                       ("norm2", "<f8"), ("r0", "<f8"), ("l", "<i4"), ("color", "<i4"),
                       ("n_jumps", "<i4"), ("n_steps_exec", "<i4"), ("flags", "<i4"),
@@ -109,6 +112,9 @@ def lib():
         L.oqt_vacuum_steps.argtypes = [C.POINTER(Params)]
         L.oqt_vacuum_steps.restype = C.c_int
         L.oqt_start_state.argtypes = [C.POINTER(Params), C.POINTER(Init), cd]
+        L.oqt_trajectory_traced.argtypes = [C.POINTER(Params), C.POINTER(Init), C.POINTER(Medium), C.c_uint64,
+                                            C.POINTER(Obs), C.POINTER(Obs), cd, C.c_int, C.c_void_p, C.c_int,
+                                            C.POINTER(C.c_int)]
         L.oqt_kappa_fit.argtypes = [C.c_int, C.c_double]
         L.oqt_kappa_fit.restype = C.c_double
         _lib = L
@@ -270,6 +276,18 @@ def jump_l(l: int, ul: float) -> int:
 def jump_color(g: Grid, color: int, uc: float) -> int:
     p = g.c()
     return lib().oqt_jump_color(C.byref(p), color, uc)
+
+
+def trajectory_trace(g: Grid, spec: Init, m: Medium, seed: int, every: int, cap: int = 100000):
+    """One trajectory without the rMin shortcut, with its per-step summary rows (TRACE_DTYPE)."""
+    p = g.c()
+    p.use_rmin = 0
+    o = Obs()
+    rec = np.zeros(cap, dtype=TRACE_DTYPE)
+    n = C.c_int()
+    lib().oqt_trajectory_traced(C.byref(p), C.byref(spec), C.byref(m), C.c_uint64(seed), None, C.byref(o), None,
+                                every, C.c_void_p(rec.ctypes.data), cap, C.byref(n))
+    return np.frombuffer(bytes(o), dtype=OBS_DTYPE).copy()[0], rec[: n.value].copy()
 
 
 def kappa_fit(which: int, T: float) -> float:

@@ -81,6 +81,16 @@ typedef struct {
     int l, color, n_jumps, n_steps_exec, flags, first_jump_step;
 } oqt_obs;
 
+/* one row of the per-step summary (App. C, summary.tsv): after step `step` (1-based), before a jump
+ * at that step -- the norm, colour, l, the overlaps |<nl|psi>|^2 of the normalised state (zero unless
+ * a singlet of the basis state's l), and <psi|r|psi> / <psi|psi> / <1S|r|1S> */
+typedef struct {
+    int step, color, l, flags;
+    double norm2;
+    double ov2[OQT_NBASIS];
+    double r_ratio;
+} oqt_trace_rec;
+
 /* basis order: 1S, 2S, 1P, 3S, 2P, 1D as (n, l) of the Coulomb problem */
 static const int OQT_BASIS_N[OQT_NBASIS] = {1, 2, 2, 3, 3, 3};
 static const int OQT_BASIS_L[OQT_NBASIS] = {0, 0, 1, 0, 1, 2};
@@ -531,9 +541,48 @@ void oqt_nojump_run(const oqt_params *p, const oqt_init *in, const oqt_medium *m
 
 /* one quantum trajectory with jumps (Sec. 3.5 item 4).  nojump (may be NULL) is the zeroth
  * trajectory of the same initial state and medium; its norm is p_NoJump = rMin. */
+/* the summary row of the state u (end of step `step`) in colour c, angular momentum l */
+static void oqt_trace_row(const oqt_params *p, const oqt_basis *b, const double complex *u, int c, int l,
+                          int step, double n2, oqt_trace_rec *rec)
+{
+    int N = p->N;
+    double dr = p->L / N;
+    memset(rec, 0, sizeof(*rec));
+    rec->step = step; rec->color = c; rec->l = l; rec->norm2 = n2;
+    double rr = 0, r1s = 0;
+    for (int j = 1; j < N; j++) {
+        double rj = j * dr;
+        rr += rj * (creal(u[j]) * creal(u[j]) + cimag(u[j]) * cimag(u[j]));
+        r1s += rj * b->phi[j] * b->phi[j];                       /* basis state 0 is 1S */
+    }
+    rec->r_ratio = (rr * dr / n2) / (r1s * dr);
+    for (int s = 0; s < OQT_NBASIS; s++) {
+        if (c != 0 || l != OQT_BASIS_L[s]) continue;
+        double complex ov = 0;
+        for (int j = 1; j < N; j++) ov += b->phi[(size_t)s * N + j] * u[j];
+        ov *= dr;
+        rec->ov2[s] = (creal(ov) * creal(ov) + cimag(ov) * cimag(ov)) / n2;
+    }
+}
+
+/* oqt_trajectory with the per-step summary: every `every` steps and after the last step (before a
+ * jump at that step), up to cap rows in rec; *n_rec rows written.  A trajectory resolved by the rMin
+ * shortcut or by r_max evolves nothing and writes no row. */
+void oqt_trajectory_traced(const oqt_params *p, const oqt_init *in, const oqt_medium *m, uint64_t seed,
+                           const oqt_obs *nojump, oqt_obs *o, double complex *u_final, int every,
+                           oqt_trace_rec *rec, int cap, int *n_rec);
+
 void oqt_trajectory(const oqt_params *p, const oqt_init *in, const oqt_medium *m, uint64_t seed,
                     const oqt_obs *nojump, oqt_obs *o, double complex *u_final)
 {
+    oqt_trajectory_traced(p, in, m, seed, nojump, o, u_final, 0, NULL, 0, NULL);
+}
+
+void oqt_trajectory_traced(const oqt_params *p, const oqt_init *in, const oqt_medium *m, uint64_t seed,
+                           const oqt_obs *nojump, oqt_obs *o, double complex *u_final, int every,
+                           oqt_trace_rec *rec, int cap, int *n_rec)
+{
+    if (n_rec) *n_rec = 0;
     int N = p->N;
     double dr = p->L / N;
     memset(o, 0, sizeof(*o));
@@ -581,6 +630,8 @@ void oqt_trajectory(const oqt_params *p, const oqt_init *in, const oqt_medium *m
         oqt_make_step(&w, u);
         o->n_steps_exec = n + 1;
         double n2 = oqt_norm2(p, u);
+        if (every > 0 && ((n + 1) % every == 0 || n + 1 == ns) && *n_rec < cap)
+            oqt_trace_row(p, &b, u, c, l, n + 1, n2, &rec[(*n_rec)++]);
         if (!isfinite(n2)) { o->flags |= OQT_F_NONFINITE; oqt_zero_observables(o); ended = 1; break; }
         if (fabs(n2 - r) < OQT_BORDERLINE_EPS) o->flags |= OQT_F_BORDERLINE;
         if (n2 <= r) {                                        /* a jump is triggered */

@@ -313,6 +313,41 @@ def test_kappa_fit_medium_decays_with_kappa_of_T(oracle_lib, which):
     assert abs(rates[1] / (gams[1] * k[0] / k[1]) - 1) > 0.15            # ... and the early value is wrong late
 
 
+def test_summary_trace_coulomb_r_ratios(oracle_lib):
+    """The per-step summary (App. C summary.tsv): R = <psi|r|psi>/<1S|r|1S> of a Coulomb state in a
+    medium without kappa and gamma is the closed-form <r>_nl / <r>_1S = (3n^2 - l(l+1)) / 3, its own
+    overlap |<nl|psi>|^2 stays 1; rows every `every` steps and after the last."""
+    o = oracle_lib
+    g = o.Grid(N=2048, L=60.0, dt=0.001)
+    m = o.medium(0.4, 0.6, 0.39, 0.0, 0.0)
+    for s, (n, l) in enumerate(((1, 0), (2, 0), (2, 1), (3, 0), (3, 1), (3, 2))):
+        ob, rec = o.trajectory_trace(g, o.init_spec("coulomb", 0.0, n, l, 0), m, 5, every=100)
+        assert list(rec["step"]) == [100, 200, ob["n_steps_exec"]]
+        assert np.abs(rec["r_ratio"] - (3 * n * n - l * (l + 1)) / 3.0).max() < 1e-4 * n * n
+        assert np.abs(rec["ov2"][:, s] - 1).max() < 1e-5
+        assert np.abs(rec["norm2"] - 1).max() < 1e-12 and (rec["color"] == 0).all() and (rec["l"] == l).all()
+
+
+def test_summary_trace_follows_the_trajectory(oracle_lib):
+    """The summary rows of a trajectory with jumps: before the first jump the norm is the no-jump
+    norm history at those steps (the same evolution), and the rows' (colour, l) change at the jumps."""
+    o = oracle_lib
+    g = o.Grid(N=64, L=2.5, dt=0.001)
+    spec = o.init_spec("gauss", 0.3, 1, 0, 0)
+    m = o.medium(T0=0.5, tau0=0.6, Tf=0.3, kappa_hat=6.0, gamma_hat=-1.0)
+    for seed in range(40):
+        ob, rec = o.trajectory_trace(g, spec, m, seed, every=10)
+        if ob["n_jumps"] >= 2:
+            break
+    assert ob["n_jumps"] >= 2
+    fj = ob["first_jump_step"]
+    _, h = o.evolve_nojump(g, o.initial_state(g, spec), 0, 0, m, 0, fj + 1)
+    pre = rec[rec["step"] <= fj + 1]
+    assert len(pre) >= 3 and np.array_equal(pre["norm2"], h[pre["step"] - 1])
+    post = rec[rec["step"] > fj + 1]
+    assert (post["color"] == 1).any() and (pre["color"] == 0).all()
+
+
 def test_table_profile_linear_pieces_and_end(oracle_lib):
     """Tabulated T(tau) (Table 1 temperatureEvolution 1/2; App. B formats): step n uses T linearly
     interpolated at tau_n = tau_1 + n dt hbar c; the evolution ends at the first crossing of Tf
