@@ -38,7 +38,7 @@ namespace qt {
 // V selects the launch variant (fused_launch.cuh); variants 2 and 3 use radix 8 for N >= 1024:
 // twice the threads per trajectory, half the registers per thread, one more FFT pass.
 template <int N, int V = 0> struct FusedPlan {
-    static constexpr int R = (N <= 32) ? 4 : (N <= 512) ? 8 : (V >= 2 ? 8 : 16);
+    static constexpr int R = (N <= 32) ? 4 : (N <= 512) ? 8 : (V == 2 || V == 3 ? 8 : 16);
     static constexpr int G = N / (2 * R);        // threads per trajectory
     static constexpr int NR = N / R;             // stride of a first/last-pass butterfly
     static constexpr int MID = N / (R * R);      // product of the middle radices
@@ -213,6 +213,14 @@ __device__ __forceinline__ float k_exp(float x) { return expf(x); }
 __device__ __forceinline__ double k_exp(double x) { return exp(x); }
 __device__ __forceinline__ float k_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double k_expm1(double x) { return expm1(x); }
+
+template <typename T> __device__ __noinline__ T table_T3_far(const double *p, int len, T tau, int *seg)
+{
+    int s = *seg;
+    const T v = table_T3<T>(p, len, tau, s);
+    *seg = s;
+    return v;
+}
 
 // f1 = exp(a) exp(i pi y) - 1, the deviation from 1 of a dynamic factor, for a <= 0 (also returns
 // exp(a) - 1).
@@ -632,6 +640,63 @@ template <typename T, int N, int V> struct Pointwise {
         return slot_norm<T, G>(acc, red);
     }
 
+    // Per-step summary row of the end-of-step state e = stat1 exp(A j^2 + i pi B j^2) x, x the state
+    // before the closing half-step (A = erj K3, B = eij T3 of the step): norm, <r>, overlaps, FP64
+    // accumulation; thread 0 writes the row.  One pass for the norm and <r> and one per basis state
+    // of the same l, so that few values stay live.  Only in the traced kernel (V = 4).
+    static __device__ __forceinline__ cpx<double> end_value(const cpx<T> *buf, const Tables<T> &tb, int c, int l, int j,
+                                                            int p, T A, T B)
+    {
+        const T fj = (T)j;
+        T f1r, f1i, em1;
+        Dyn<T>::f1((A * fj) * fj, (B * fj) * fj, &f1r, &f1i, &em1);
+        const cpx<T> w = PR::mul(buf[p], stat(tb, tb.statV, c, l, j, false));
+        return mk((double)(w.x + (w.x * f1r - w.y * f1i)), (double)(w.y + (w.x * f1i + w.y * f1r)));
+    }
+
+    static __device__ void trace_row(const cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, T A, T B,
+                                     double *red, qtraj_trace_rec *out, int step)
+    {
+        double n2 = 0.0, rr = 0.0;
+        for (int k = g; k < N / 2; k += G)
+            for (int par = 0; par < 2; ++par) {
+                const int j = 2 * k + par;
+                const cpx<double> e = end_value(buf, tb, c, l, j, par ? K::odd_pos(k) : k, A, B);
+                const double m2 = e.x * e.x + e.y * e.y;
+                n2 += m2;
+                rr += (double)j * tb.dr * m2;
+            }
+        n2 = slot_sum<G>(n2, red);
+        rr = slot_sum<G>(rr, red);
+        const double dr = tb.dr;
+        if (g == 0) {
+            out->step = step;
+            out->color = c;
+            out->l = l;
+            out->flags = 0;
+            out->norm2 = n2 * dr;
+            out->r_ratio = (rr / n2) / tb.r1s;
+        }
+#pragma unroll 1
+        for (int s = 0; s < NBASIS; ++s) {
+            const int bl = s == 2 || s == 4 ? 1 : (s == 5 ? 2 : 0);
+            double vr = 0.0, vi = 0.0;
+            if (c == 0 && bl == l) {
+                for (int k = g; k < N / 2; k += G)
+                    for (int par = 0; par < 2; ++par) {
+                        const int j = 2 * k + par;
+                        const cpx<double> e = end_value(buf, tb, c, l, j, par ? K::odd_pos(k) : k, A, B);
+                        const double ph = tb.eig[(size_t)s * N + j];
+                        vr += ph * e.x;
+                        vi += ph * e.y;
+                    }
+                vr = slot_sum<G>(vr, red);
+                vi = slot_sum<G>(vi, red);
+            }
+            if (g == 0) out->ov2[s] = (vr * vr + vi * vi) * dr / n2;
+        }
+    }
+
     // Undoes the start half-step applied by a mode-1 factor, x <- conj(stat1(c,l)) exp(A j^2 + i pi B j^2) x
     // with A = -er_b dr^2 and B = -ei_b dr^2 / pi: the end-of-step state of a trajectory that stops
     // at a jump cap.
@@ -713,7 +778,7 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
 // for 768 and 1024.  FP64 holds twice the state and takes what the compiler needs.
 template <typename T, int N, int V> struct FusedBounds {
     static constexpr int G = FusedPlan<N, V>::G;
-    static constexpr int THREADS = V == 0 ? (N == 4096 ? 384 : 512) : V == 1 ? 640 : V == 2 ? 768 : 1024;
+    static constexpr int THREADS = (V == 0 || V == 4) ? (N == 4096 ? 384 : 512) : V == 1 ? 640 : V == 2 ? 768 : 1024;
     static constexpr int MB = THREADS / G > 32 ? 32 : (THREADS / G > 0 ? THREADS / G : 1);
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? MB : 1;
 };
@@ -769,14 +834,18 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         const double r0 = a.nojump ? 0.0 : dw.r;
         double thr = a.nojump ? -1.0 : dw.r;
         int nj = 0, flags = 0, fj = -1, ended = 0, executed = 0;
+        const bool traced = V == 4 && a.trace_every > 0 && t < a.trace_n;
+        int nrec = 0;
         const int ns = d.n_steps;
         // per-step scalars in the working precision: T^3 = A / (tau0 + n dtau)
         const T mA = (T)md.A, mtau0 = (T)md.tau0, mdtau = (T)md.dtau;
-        const double *prof = md.kind == 1 ? tb.prof + 2 * (size_t)md.tab_off : nullptr;
+        const bool tabulated = md.kind == 1;
         int seg = 0;
-        // T(tau_n)^3: Bjorken, or the table at tau_n = tau_1 + n dtau
+        // T(tau_n)^3: Bjorken, or the table at tau_n = tau_1 + n dtau (out of line: rare, and inline it
+        // would hold registers in the step loop)
         auto T3_of = [&](int n) -> T {
-            return prof ? table_T3<T>(prof, md.tab_len, mtau0 + (T)n * mdtau, seg) : mA / (mtau0 + (T)n * mdtau);
+            return tabulated ? table_T3_far<T>(tb.prof + 2 * (size_t)md.tab_off, md.tab_len, mtau0 + (T)n * mdtau, &seg)
+                             : mA / (mtau0 + (T)n * mdtau);
         };
         T T3b = T3_of(0);
         T K3b = kappa_T3<T>(md.kfit, T3b);   // kappa_hat(T) T^3 when kappa_hat follows a lattice fit
@@ -795,6 +864,14 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             for (int h = 0; h < 2; ++h) K::dst(x, buf, tb, g, wtot, tw1, tw2, h == 1);
             executed = n + 1;
             const T erj = (T)md.erj[c], eij = (T)md.eij[c];
+            if constexpr (V == 4) {   // the traced twin of variant 0: per-step summary rows
+                if (traced && ((n + 1) % a.trace_every == 0 || last) && nrec < a.trace_cap) {
+                    PW::trace_row(buf, tb, g, c, l, erj * K3a, eij * T3a, red,
+                                  a.trace + (size_t)t * a.trace_cap + nrec, n + 1);
+                    ++nrec;
+                    __syncthreads();
+                }
+            }
             const T Tsum = last ? T3a : T3a + T3b, Ksum = last ? K3a : K3a + K3b;
             const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Ksum, eij * Tsum,
                                          last ? (T)0 : erj * (K3a - K3b), red) * dr;
@@ -909,6 +986,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             o.flags = flags;
             o.first_jump_step = fj;
             a.obs[t] = o;
+            if (traced) a.trace_cnt[t] = nrec;
         }
         __syncthreads();
     }
