@@ -269,6 +269,31 @@ def run_ours(args):
         print(json.dumps(result))
 
 
+def run_serving_sweep(args):
+    """The first --serving-requests requests of the stream replayed at each offered rate of
+    --serving-sweep (the arrival gaps of the 200 req/s stream rescaled): latency against offered load,
+    down to a rate one GPU sustains.  One JSON line per rate."""
+    import torch
+
+    from paper_2107_06147_gb300 import inputs, serving
+    for rate in [float(r) for r in args.serving_sweep.split(",")]:
+        st = inputs.serving_stream(n_requests=args.serving_requests, rate_hz=200.0, seed=1)
+        arrival = st["arrival_s"] * (200.0 / rate)
+        reqs = serving.requests_from_stream(st)
+        Ns = sorted(set(int(n) for n in st["N"]))
+        srv = serving.Server(Ns=tuple(Ns), slots_per_n=2, wave_mult=4)
+        torch.cuda.synchronize()
+        wall = srv.run_stream(reqs, arrival)
+        srv.close()
+        lat = serving.latency_stats(reqs)
+        steps = int(sum(int(r.obs["n_steps_exec"].sum()) for r in reqs))
+        print(json.dumps({"serving_sweep": True, "offered_rate_hz": rate, "requests": len(reqs),
+                          "latency_p50_s": round(lat["p50_s"], 3), "latency_p99_s": round(lat["p99_s"], 3),
+                          "latency_mean_s": round(lat["mean_s"], 3), "wall_s": round(wall, 3),
+                          "completed_rate_hz": round(len(reqs) / wall, 4), "traj_steps_per_s": round(steps / wall, 1),
+                          "trajectories": int(sum(r.ntraj for r in reqs)), "traj_steps": steps}), flush=True)
+
+
 def run_serving(args):
     """p50/p99 request latency of the continuous-batching loop on the first --serving-requests of the
     Poisson request stream (200 req/s, seed 1; initial state in {1S, 2S, 1P}, kappa ~ U[3,7],
@@ -422,10 +447,17 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
     ap.add_argument("--profile-steps", type=int, default=1000)
+    ap.add_argument("--serving-sweep", default="", metavar="RATES",
+                    help="comma-separated offered rates (req/s): replay the --serving-requests prefix at each")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NTRAJ",
                     help="paired FP64/FP32 study on NTRAJ trajectories of N=8192, L=80, dt=0.0005 (no timing line)")
     args = ap.parse_args()
     args.batch_given = any(a.startswith("--batch") for a in sys.argv[1:])
+    if args.serving_sweep:
+        from paper_2107_06147_gb300 import build
+        build.build()
+        run_serving_sweep(args)
+        return
     if args.precision_study:
         from paper_2107_06147_gb300 import build, inputs, precision
         build.build()
