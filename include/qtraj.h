@@ -151,6 +151,28 @@ qtraj_status qtraj_init(qtraj_ctx *ctx, void *d_workspace, size_t bytes, int n_t
  * bound n_traj or an index is out of range. */
 qtraj_status qtraj_set_spec_idx(qtraj_ctx *ctx, const int *spec_idx, int n);
 
+/* One row of the per-step summary of a trajectory (App. C, summary.tsv): after step `step` (1-based
+ * count of the medium's steps), before a jump triggered at that step -- the discrete norm^2, the
+ * colour and l, the overlaps |<nl|psi>|^2 / norm^2 with the Coulomb basis (zero unless a singlet of
+ * the basis state's l) and R = <psi|r|psi> / norm^2 / <1S|r|1S>.  80 bytes. */
+typedef struct {
+    int step, color, l, flags;
+    double norm2;
+    double ov2[6];
+    double r_ratio;
+} qtraj_trace_rec;
+
+/* Turns the per-step summary on (every > 0) or off (every = 0) for the evolves that follow: the first
+ * n_traced trajectories of each batch write a row every `every` steps and after their last step, at
+ * most max_records rows each, to d_records[t * max_records + i]; d_counts[t] receives the number of
+ * rows (the evolve clears d_counts[0 .. n_traced) first).  Both are caller device buffers that must
+ * stay valid while those evolves run.  A trajectory resolved without evolving (rMin shortcut,
+ * r_max) writes no row.  Fused form only (EINVAL for the plain form); while it is on, evolves run a
+ * traced copy of the fused kernel (variant 0's plan), which at each recorded step of a traced
+ * trajectory makes one more pass over the state per quantity. */
+qtraj_status qtraj_set_trace(qtraj_ctx *ctx, int every, int n_traced, int max_records, qtraj_trace_rec *d_records,
+                             int *d_counts);
+
 /* Sets the context's profile store: n_points (tau [fm/c], T [GeV]) points from host arrays,
  * referred to by kind-1 media through (table_offset, table_len).  Several profiles share the store
  * back to back.  Waits for the context's queued work, then uploads (synchronous); replaces the

@@ -105,6 +105,10 @@ struct qtraj_ctx {
     bool ic_cplx = false;   // ic holds complex states (after a vacuum evolution)
     double *prof = nullptr; // profile store of tabulated media: (tau, T) pairs
     std::vector<double> prof_host;
+    double r1s = 1.0;       // <1S|r|1S> on the grid
+    qtraj_trace_rec *trace = nullptr;   // per-step summary (caller buffers), off when trace_every == 0
+    int *trace_cnt = nullptr;
+    int trace_every = 0, trace_n = 0, trace_cap = 0;
     int n_spec = 0;
     std::vector<qtraj_init_spec> specs;
     std::vector<int> spec_idx;
@@ -234,6 +238,7 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     t.r_max = c->p.r_max;
     t.ic_cplx = c->ic_cplx ? 1 : 0;
     t.prof = c->prof;
+    t.r1s = c->r1s;
     return t;
 }
 
@@ -445,6 +450,13 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     c->dr = L / N;
     c->p = p;
     c->a0 = 2.0 / (M * (p.Nc * p.Nc - 1.0) / (2.0 * p.Nc) * p.alpha_s);
+    if (std::isfinite(c->a0)) {
+        std::vector<double> phi;
+        coulomb_u(N, c->dr, c->a0, 1, 0, phi);
+        double r1 = 0.0;
+        for (int j = 1; j < N; ++j) r1 += j * c->dr * phi[j] * phi[j];
+        c->r1s = r1 * c->dr;
+    }
     qtraj_status st = QTRAJ_OK;
     auto bail = [&](qtraj_status s) {
         qtraj_destroy(c);
@@ -604,6 +616,25 @@ qtraj_status qtraj_set_profiles(qtraj_ctx *c, const double *tau, const double *T
     return QTRAJ_OK;
 }
 
+qtraj_status qtraj_set_trace(qtraj_ctx *c, int every, int n_traced, int max_records, qtraj_trace_rec *d_records,
+                             int *d_counts)
+{
+    g_err.clear();
+    if (!c) return fail(QTRAJ_EINVAL, "null argument");
+    if (every < 0) return fail(QTRAJ_EINVAL, "every must be >= 0");
+    if (every > 0) {
+        if (c->p.form != QTRAJ_FUSED) return fail(QTRAJ_EINVAL, "the per-step summary needs the fused form");
+        if (n_traced <= 0 || max_records <= 0 || !d_records || !d_counts)
+            return fail(QTRAJ_EINVAL, "n_traced, max_records and the buffers are required");
+    }
+    c->trace_every = every;
+    c->trace_n = every > 0 ? n_traced : 0;
+    c->trace_cap = every > 0 ? max_records : 0;
+    c->trace = every > 0 ? d_records : nullptr;
+    c->trace_cnt = every > 0 ? d_counts : nullptr;
+    return QTRAJ_OK;
+}
+
 qtraj_status qtraj_set_spec_idx(qtraj_ctx *c, const int *spec_idx, int n)
 {
     g_err.clear();
@@ -707,6 +738,14 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
 
     LaunchArgs ga{d_gt, n_groups, d_gobs, nullptr, d_ctr, d_status, nullptr, 1};
     LaunchArgs ma{d_tr, batch, d_obs, d_gobs, d_ctr, d_status, d_states, 0};
+    if (c->trace_every > 0 && c->p.form == QTRAJ_FUSED) {
+        ma.trace = c->trace;
+        ma.trace_cnt = c->trace_cnt;
+        ma.trace_every = c->trace_every;
+        ma.trace_n = c->trace_n;
+        ma.trace_cap = c->trace_cap;
+        CK(cudaMemsetAsync(c->trace_cnt, 0, sizeof(int) * (size_t)c->trace_n, s));
+    }
     CK(cudaEventRecord(c->ev0, s));
     if (c->p.form == QTRAJ_PLAIN) {
         const size_t nN = (size_t)c->n_traj * N;

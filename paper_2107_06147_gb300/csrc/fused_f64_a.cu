@@ -41,14 +41,22 @@ cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int 
 cudaError_t fused_launch_f64(int N, const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
                              cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
+    if (a.trace_every > 0) variant = 0;   // the per-step summary runs the traced twin of variant 0
     switch (N) {
-    case 16: return go<16, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 32: return go<32, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 64: return go<64, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 128: return go<128, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 256: return go<256, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 512: return go<512, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 1024: return go<1024, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 16: return a.trace_every > 0 ? go<16, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<16, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 32: return a.trace_every > 0 ? go<32, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<32, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 64: return a.trace_every > 0 ? go<64, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<64, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 128: return a.trace_every > 0 ? go<128, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<128, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 256: return a.trace_every > 0 ? go<256, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<256, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 512: return a.trace_every > 0 ? go<512, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<512, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 1024: return a.trace_every > 0 ? go<1024, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<1024, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
     default: return fused_launch_f64_b(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);
     }
 }

@@ -39,8 +39,10 @@ cudaError_t go(const Tables<double> &tb, const LaunchArgs &a, int sm_count, int 
 cudaError_t fused_launch_f64_c(int N, const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
                              cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
+    if (a.trace_every > 0) variant = 0;   // the per-step summary runs the traced twin of variant 0
     switch (N) {
-    case 8192: return go<8192, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 8192: return a.trace_every > 0 ? go<8192, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : go<8192, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -320,6 +320,7 @@ struct TrajDev {
 };
 
 static_assert(sizeof(qtraj_obs) == 184, "qtraj_obs layout");
+static_assert(sizeof(qtraj_trace_rec) == 80, "qtraj_trace_rec layout");
 
 // Read-only context tables (device pointers) and scalars.
 template <typename T> struct Tables {
@@ -343,6 +344,7 @@ template <typename T> struct Tables {
     double r_max;
     int ic_cplx;
     const double *prof;    // profile store: (tau, T) pairs of the tabulated media
+    double r1s;            // <1S|r|1S> on the grid (discrete), the unit of the summary's R
 };
 
 // per-launch arguments of both forms
@@ -355,6 +357,9 @@ struct LaunchArgs {
     int *status;            // bit 0: a non-finite norm was seen
     double *states;         // optional final states [n_traj][N] complex128
     int nojump;             // 1: no-jump mode (trajectory t = group t, never jumps)
+    qtraj_trace_rec *trace; // per-step summary rows [trace_n][trace_cap] (traced kernel; off if trace_every 0)
+    int *trace_cnt;         // rows written per traced trajectory
+    int trace_every, trace_n, trace_cap;
 };
 
 // static part of the half-step space kernel for (colour, l, j); rows beyond the table are

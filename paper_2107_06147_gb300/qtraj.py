@@ -71,6 +71,11 @@ TRAJ_DESC_DTYPE = np.dtype([("N", "<i4"), ("spec", "<i4"), ("kind", "<i4"), ("_p
                             ("table_offset", "<i4"), ("table_len", "<i4"), ("seed", "<u8")])
 assert TRAJ_DESC_DTYPE.itemsize == C.sizeof(TrajDesc) == 72
 
+# qtraj_trace_rec: one row of a trajectory's per-step summary
+TRACE_DTYPE = np.dtype([("step", "<i4"), ("color", "<i4"), ("l", "<i4"), ("flags", "<i4"), ("norm2", "<f8"),
+                        ("ov2", "<f8", NBASIS), ("r_ratio", "<f8")])
+assert TRACE_DTYPE.itemsize == 80
+
 OBS_DTYPE = np.dtype([("surv", "<f8", NBASIS), ("ov_re", "<f8", NBASIS), ("ov_im", "<f8", NBASIS),
                       ("norm2", "<f8"), ("r0", "<f8"), ("l", "<i4"), ("color", "<i4"), ("n_jumps", "<i4"),
                       ("n_steps_exec", "<i4"), ("flags", "<i4"), ("first_jump_step", "<i4")])
@@ -85,6 +90,7 @@ _PROTOS = {
     "qtraj_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.POINTER(InitSpec), C.c_int,
                              C.POINTER(C.c_int)]),
     "qtraj_set_spec_idx": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int]),
+    "qtraj_set_trace": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_set_profiles": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
     "qtraj_evolve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Medium), C.c_int, C.POINTER(C.c_int),
                                C.POINTER(C.c_uint64), C.c_void_p]),
@@ -219,6 +225,29 @@ class Engine:
             idx = self._spec_idx.ctypes.data_as(C.POINTER(C.c_int))
         _check(self.lib.qtraj_init(self.ctx, C.c_void_p(ptr), have, n_traj, arr, len(specs), idx), self.ctx)
         self.n_traj = n_traj
+
+    def set_trace(self, every: int, n_traced: int = 1, max_records: int = 1024):
+        """Per-step summary rows for the first n_traced trajectories of later evolves (every = 0: off).
+        The row buffers are torch device tensors held by the engine."""
+        import torch
+        if every <= 0:
+            _check(self.lib.qtraj_set_trace(self.ctx, 0, 0, 0, None, None), self.ctx)
+            self._trace = None
+            return
+        rec = torch.zeros(n_traced * max_records * TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(n_traced, dtype=torch.int32, device="cuda")
+        _check(self.lib.qtraj_set_trace(self.ctx, every, n_traced, max_records, C.c_void_p(rec.data_ptr()),
+                                        C.c_void_p(cnt.data_ptr())), self.ctx)
+        self._trace = (rec, cnt, n_traced, max_records)
+
+    def trace(self) -> list:
+        """The summary rows of each traced trajectory of the last evolve (synchronises the device)."""
+        import torch
+        rec, cnt, n, cap = self._trace
+        torch.cuda.synchronize()
+        r = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=TRACE_DTYPE).reshape(n, cap)
+        c = cnt.cpu().numpy()
+        return [r[i, : c[i]].copy() for i in range(n)]
 
     def set_profiles(self, tau, T):
         """Sets the profile store of tabulated media: points (tau [fm/c], T [GeV]); synchronous."""

@@ -316,6 +316,47 @@ def test_tabulated_profile_errors(q):
     e.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_summary_trace(q, precision):
+    """Per-step summary rows (App. C summary.tsv; the traced twin of the fused kernel) against the
+    oracle's rows for the same trajectories: steps, colour and l equal, norm, overlaps and
+    <r>/<r>_1S to the form's precision (FP32: on trajectories whose jump sequence is the oracle's)."""
+    import oracle as o
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=64, n_traj=16, seed=51)
+    g, inits, media = oracle_inputs(w)
+    e = q.Engine(q.Config(N=64, L=w.grid.L, dt=w.grid.dt, precision=precision, use_rmin=0))
+    e.init([q.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits], 16, w.init_idx)
+    e.set_trace(every=50, n_traced=8, max_records=256)
+    e.evolve([q.medium(m.T0, m.tau0, m.Tf, m.kappa_hat, m.gamma_hat) for m in w.media], w.seeds, w.medium_idx)
+    obs = e.observables()
+    rows = e.trace()
+    e.set_trace(0)
+    e.close()
+    n_cmp = 0
+    for t in range(8):
+        ob, ref = o.trajectory_trace(g, inits[w.init_idx[t]], media[w.medium_idx[t]], int(w.seeds[t]), every=50)
+        got = rows[t]
+        if precision == 1 and (ob["n_jumps"] != obs["n_jumps"][t] or ob["first_jump_step"] != obs["first_jump_step"][t]):
+            continue
+        n_cmp += 1
+        assert len(got) == len(ref) > 0
+        for f in ("step", "color", "l"):
+            assert np.array_equal(got[f], ref[f]), (t, f)
+        tol = 1e-9 if precision == 0 else 2e-4
+        for f in ("norm2", "r_ratio"):
+            assert np.allclose(got[f], ref[f], rtol=tol, atol=0), (t, f, got[f], ref[f])
+        assert np.allclose(got["ov2"], ref["ov2"], rtol=tol, atol=tol * 1e-3), t
+    assert n_cmp >= 6
+
+
+def test_trace_needs_fused_form(q):
+    e = q.Engine(q.Config(N=64, L=2.5, dt=0.001, form=q.PLAIN))
+    with pytest.raises(q.QtrajError):
+        e.set_trace(every=10, n_traced=1, max_records=4)
+    e.close()
+
+
 def test_static_entry_rejects_vacuum_evolution(q):
     import ctypes as C
     import torch
