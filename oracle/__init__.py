@@ -6,6 +6,7 @@ and this package imports nothing from it.
 
 ``qtraj_oracle.c`` holds the method (own radix-2 FFT, own Philox4x32-10, the Strang step, the
 waiting-time jumps, the observables); ``core.py`` is its ctypes wrapper; ``lindblad.py`` is a
-brute-force density-matrix integrator used only to pin the oracle's unravelling.
+brute-force density-matrix integrator used only to pin the oracle's unravelling; ``eigen.py``
+diagonalises the dense discretised vacuum Hamiltonian for the numerical eigenstates.
 """
 from .core import *  # noqa: F401,F403

@@ -37,12 +37,12 @@ class Params(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_double), ("dt", C.c_double), ("M", C.c_double),
                 ("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int),
                 ("max_jumps", C.c_int), ("r_max", C.c_double), ("l_cap", C.c_int),
-                ("use_rmin", C.c_int), ("t_vac", C.c_double)]
+                ("use_rmin", C.c_int), ("t_vac", C.c_double), ("basis", C.POINTER(C.c_double))]
 
 
 class Init(C.Structure):
     _fields_ = [("kind", C.c_int), ("width", C.c_double), ("n", C.c_int), ("l", C.c_int),
-                ("color", C.c_int)]
+                ("color", C.c_int), ("u0", C.POINTER(C.c_double))]
 
 
 class Medium(C.Structure):
@@ -143,14 +143,28 @@ class Grid:
     l_cap: int = -1
     use_rmin: int = 1
     t_vac: float = 0.0
+    basis: object = None          # (NBASIS, N) overlap basis (numerical eigenstates); None: analytic
 
     def c(self) -> Params:
+        b = None
+        if self.basis is not None:
+            self._basis_c = np.ascontiguousarray(self.basis, dtype=np.float64)
+            b = _dp(self._basis_c)
         return Params(self.N, self.L, self.dt, self.M, self.alpha_s, self.Nc, self.deriv_type,
-                      self.max_jumps, self.r_max, self.l_cap, self.use_rmin, self.t_vac)
+                      self.max_jumps, self.r_max, self.l_cap, self.use_rmin, self.t_vac, b)
 
 
 def init_spec(kind: str = "gauss", width: float = 0.2, n: int = 1, l: int = 0, color: int = 0) -> Init:
-    return Init(0 if kind == "gauss" else 1, width, n, l, color)
+    return Init(0 if kind == "gauss" else 1, width, n, l, color, None)
+
+
+def given_state(u0, n: int, l: int, color: int = 0) -> Init:
+    """Initial state kind 2: the given (numerical) eigenstate (n, l), discretely normalised; the
+    record keeps its own copy of the values alive."""
+    a = np.ascontiguousarray(np.real(u0), dtype=np.float64)
+    s = Init(2, 0.0, n, l, color, _dp(a))
+    s._keep = a
+    return s
 
 
 def medium(T0=0.425, tau0=0.6, Tf=0.25, kappa_hat=5.0, gamma_hat=0.0) -> Medium:

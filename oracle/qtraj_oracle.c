@@ -61,9 +61,12 @@ typedef struct {
     int l_cap;        /* < 0: none; a jump to l > l_cap ends the trajectory with zero overlaps */
     int use_rmin;     /* 1: rMin shortcut */
     double t_vac;     /* vacuum evolution before the medium, GeV^-1 (Table 1: tmed - t0); 0: none */
+    const double *basis; /* OQT_NBASIS x N overlap basis (numerical eigenstates), NULL: analytic Coulomb */
 } oqt_params;
 
-typedef struct { int kind; double width; int n, l, color; } oqt_init;  /* kind 0 Gaussian, 1 Coulomb */
+/* kind 0 Gaussian, 1 analytic Coulomb eigenstate, 2 a given (numerical) eigenstate in u0 (N values,
+ * discretely normalised) */
+typedef struct { int kind; double width; int n, l, color; const double *u0; } oqt_init;
 /* kind 0: Bjorken T0 (tau0/tau)^{1/3} from tau0; kind 1: T(tau) interpolated linearly in the table
  * (tab_tau[i], tab_T[i]), i < tab_n, tau ascending (fm/c), from tab_tau[0] (Table 1
  * temperatureEvolution 1/2; the file formats of App. B).  Both end once T < Tf. */
@@ -324,6 +327,11 @@ void oqt_eigenstate(const oqt_params *p, int n, int l, double *phi)
 void oqt_initial_state(const oqt_params *p, const oqt_init *in, double complex *u)
 {
     double dr = p->L / p->N;
+    if (in->kind == 2) {
+        u[0] = 0;
+        for (int j = 1; j < p->N; j++) u[j] = in->u0[j];
+        return;
+    }
     if (in->kind == 1) {
         double *phi = malloc(sizeof(double) * p->N);
         oqt_eigenstate(p, in->n, in->l, phi);
@@ -473,11 +481,13 @@ static void oqt_basis_init(oqt_basis *b, const oqt_params *p, const oqt_init *in
     double complex *u0 = malloc(sizeof(double complex) * N);
     oqt_start_state(p, in, u0);          /* the survival ratios refer to the state entering the medium */
     for (int s = 0; s < OQT_NBASIS; s++) {
-        oqt_eigenstate(p, OQT_BASIS_N[s], OQT_BASIS_L[s], b->phi + (size_t)s * N);
-        /* zero unless the initial state is a singlet of the same l; an analytic Coulomb initial
-         * state is orthogonal to the other n of its l */
-        int zero = in->color != 0 || in->l != OQT_BASIS_L[s] ||
-                   (in->kind == 1 && in->n != OQT_BASIS_N[s]);
+        if (p->basis) memcpy(b->phi + (size_t)s * N, p->basis + (size_t)s * N, sizeof(double) * N);
+        else oqt_eigenstate(p, OQT_BASIS_N[s], OQT_BASIS_L[s], b->phi + (size_t)s * N);
+        /* zero unless the initial state is a singlet of the same l; an eigenstate of the basis' own
+         * kind (analytic Coulomb, or numerical with a numerical basis) is orthogonal to the basis
+         * states of other n of its l */
+        int same_family = (in->kind == 1 && !p->basis) || (in->kind == 2 && p->basis);
+        int zero = in->color != 0 || in->l != OQT_BASIS_L[s] || (same_family && in->n != OQT_BASIS_N[s]);
         b->ov0_zero[s] = zero;
         double complex o = 0;
         if (!zero)

@@ -348,6 +348,51 @@ def test_summary_trace_follows_the_trajectory(oracle_lib):
     assert (post["color"] == 1).any() and (pre["color"] == 0).all()
 
 
+def test_numerical_eigenstates_energies_and_propagation(oracle_lib):
+    """Numerical eigenstates of the discretised vacuum Hamiltonian (initType 100 / ProjType 1):
+    their energies approach E_n = -M (C_F alpha_s)^2 / (4 n^2) under refinement, and they are
+    eigenstates of the oracle's own propagator: after 1000 vacuum steps a numerical 1S has turned
+    its phase by -E t and kept |<phi|psi>| = 1 to O(dt^2), far closer than the analytic 1S (which
+    the grid's Hamiltonian does not hold exactly)."""
+    from oracle import eigen
+    o = oracle_lib
+    M, alpha = 4.65, 4.0 / 3.0 * 0.3
+    errs = {}
+    for N in (512, 1024):
+        g = o.Grid(N=N, L=40.0, dt=0.001)
+        for l, m in ((0, 2), (1, 1)):
+            lam, _ = eigen.vacuum_eigenstates(g, l, m)
+            for k in range(m):
+                n = l + 1 + k
+                errs[(N, n, l)] = abs(lam[k] + M * alpha ** 2 / (4 * n * n)) / (M * alpha ** 2 / (4 * n * n))
+    assert errs[(1024, 1, 0)] < errs[(512, 1, 0)] and errs[(1024, 1, 0)] < 2e-3
+    assert errs[(1024, 2, 0)] < 2e-3 and errs[(1024, 2, 1)] < 2e-3
+    m0 = o.medium(kappa_hat=0.0, gamma_hat=0.0)
+    perr = []
+    for dt in (0.001, 0.0005):
+        g = o.Grid(N=512, L=20.0, dt=dt)
+        lam, v = eigen.vacuum_eigenstates(g, 0, 1)
+        dr = g.L / g.N
+        nst = int(round(1.0 / dt))
+        u, _ = o.evolve_nojump(g, v[0].astype(np.complex128), 0, 0, m0, 0, nst)
+        A = dr * np.dot(v[0], u)
+        assert abs(abs(A) - 1) < 1e-7
+        perr.append(abs(-np.angle(A) / (nst * dt) - lam[0]) / abs(lam[0]))
+    assert perr[0] < 3e-6 and 3.0 < perr[0] / perr[1] < 5.0        # the splitting's O(dt^2) only
+    g = o.Grid(N=512, L=20.0, dt=0.001)
+    lam, v = eigen.vacuum_eigenstates(g, 0, 1)
+    dr = g.L / g.N
+    u, _ = o.evolve_nojump(g, v[0].astype(np.complex128), 0, 0, m0, 0, 1000)
+    A = dr * np.dot(v[0], u)
+    phi = o.eigenstate(g, 1, 0)
+    ua, _ = o.evolve_nojump(g, phi.astype(np.complex128), 0, 0, m0, 0, 1000)
+    assert abs(abs(dr * np.dot(phi, ua)) - 1) > 100 * abs(abs(A) - 1)
+    # a numerical 1S start, measured in the numerical basis, keeps S(1S) = 1 in vacuum
+    g.basis = eigen.numerical_basis(g)
+    rec = o.nojump_run(g, o.given_state(g.basis[0], 1, 0), o.medium(0.4, 0.6, 0.39, 0.0, 0.0))
+    assert abs(rec["surv"][0] - 1) < 1e-7 and abs(rec["surv"][1]) < 1e-12
+
+
 def test_table_profile_linear_pieces_and_end(oracle_lib):
     """Tabulated T(tau) (Table 1 temperatureEvolution 1/2; App. B formats): step n uses T linearly
     interpolated at tau_n = tau_1 + n dt hbar c; the evolution ends at the first crossing of Tf
