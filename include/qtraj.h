@@ -71,10 +71,16 @@ typedef struct {
                         result is the state every trajectory starts the medium with and the
                         reference of the survival ratios.  Runs in the fused form of the context's
                         precision, so an FP64 context with t_vacuum > 0 needs N <= 8192. */
+    int basis;       /* overlap basis of the observables (App. C; Sec. 2.5): 0 = the analytic Coulomb
+                        states u_nl (a0 = 2/(M C_F alpha_s)), discretely normalised; 1 = the numerical
+                        eigenstates of the discretised singlet vacuum Hamiltonian of the grid (the
+                        propagator's V and kinetic factor), computed at qtraj_create by a
+                        preconditioned block eigensolver (the paper's ProjType 1); needs alpha_s > 0. */
 } qtraj_params;
 
 /* Initial state (Table 1, initType/initWidth/initN/initL/initC): kind 0 is the Gaussian
- * u = r^{l+1} exp(-r^2/(2 width^2)); kind 1 is the Coulomb eigenstate (n, l).  color 0 = singlet,
+ * u = r^{l+1} exp(-r^2/(2 width^2)); kind 1 is the analytic Coulomb eigenstate (n, l); kind 2 is
+ * the numerical eigenstate (n, l) of the discretised singlet vacuum Hamiltonian (initType 100).  color 0 = singlet,
  * 1 = octet.  The state is normalised with the discrete norm (L/N) sum |u_j|^2 = 1 (Eq. normcond). */
 typedef struct {
     int kind;
@@ -150,6 +156,10 @@ qtraj_status qtraj_init(qtraj_ctx *ctx, void *d_workspace, size_t bytes, int n_t
  * scheduler reuse one bound workspace for batches of different composition.  EINVAL if n exceeds the
  * bound n_traj or an index is out of range. */
 qtraj_status qtraj_set_spec_idx(qtraj_ctx *ctx, const int *spec_idx, int n);
+
+/* Copies the context's overlap basis (QTRAJ_NBASIS x N doubles, the order of qtraj_obs.surv) to
+ * host memory. */
+qtraj_status qtraj_basis_get(const qtraj_ctx *ctx, double *out);
 
 /* One row of the per-step summary of a trajectory (App. C, summary.tsv): after step `step` (1-based
  * count of the medium's steps), before a jump triggered at that step -- the discrete norm^2, the

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "eigen.h"
 #include "fused_launch.cuh"
 #include "plain.cuh"
 #include "qtraj.h"
@@ -106,6 +107,7 @@ struct qtraj_ctx {
     double *prof = nullptr; // profile store of tabulated media: (tau, T) pairs
     std::vector<double> prof_host;
     double r1s = 1.0;       // <1S|r|1S> on the grid
+    std::vector<double> basis_host;   // [NBASIS][N] the overlap basis (analytic or numerical)
     qtraj_trace_rec *trace = nullptr;   // per-step summary (caller buffers), off when trace_every == 0
     int *trace_cnt = nullptr;
     int trace_every = 0, trace_n = 0, trace_cap = 0;
@@ -345,6 +347,22 @@ MediumDev encode_medium(const qtraj_ctx *c, const qtraj_medium &q)
 } // namespace
 
 namespace {
+// The m lowest numerical eigenstates of the discretised singlet vacuum Hamiltonian of angular
+// momentum l (n = l+1 .. l+m), started from the analytic Coulomb states of the same n.
+qtraj_status numerical_states(const qtraj_ctx *c, int l, int m, std::vector<std::vector<double>> &out)
+{
+    const double Nc = c->p.Nc;
+    EigenProblem ep{c->N, c->L, c->M, -(Nc * Nc - 1.0) / (2.0 * Nc) * c->p.alpha_s, c->p.deriv_type};
+    std::vector<std::vector<double>> start(m);
+    for (int k = 0; k < m; ++k) coulomb_u(c->N, c->dr, c->a0, l + 1 + k, l, start[k]);
+    std::vector<double> lam;
+    const int it = vacuum_eigenstates(ep, l, m, start, out, lam);
+    if (it < 0) return fail(QTRAJ_EINVAL, "numerical eigenstates of l = %d did not converge", l);
+    return QTRAJ_OK;
+}
+} // namespace
+
+namespace {
 // Evolves every initial state of the context in vacuum for n_vac steps (T = 0: the Coulomb and
 // centrifugal potential of its colour, no imaginary part, no jump test) with the fused kernel of the
 // context's precision, then makes the results the context's (complex) initial states and their
@@ -395,7 +413,7 @@ qtraj_status vacuum_evolution(qtraj_ctx *c, int n_specs, int n_vac)
     std::vector<int> zero((size_t)n_specs * NBASIS);
     CK(cudaMemcpy(zero.data(), c->ov0_zero, sizeof(int) * zero.size(), cudaMemcpyDeviceToHost));
     for (int b = 0; b < NBASIS; ++b) {
-        coulomb_u(N, c->dr, c->a0, BASIS_N[b], BASIS_L[b], phi);
+        phi.assign(c->basis_host.begin() + (size_t)b * N, c->basis_host.begin() + (size_t)(b + 1) * N);
         for (int s = 0; s < n_specs; ++s) {
             if (zero[(size_t)s * NBASIS + b]) continue;
             const double *u = states.data() + (size_t)s * N * 2;
@@ -441,6 +459,8 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     if (!(p.t_vacuum >= 0) || !std::isfinite(p.t_vacuum)) return fail(QTRAJ_EINVAL, "t_vacuum must be finite and >= 0");
     if (p.t_vacuum > 0 && p.precision == QTRAJ_FP64 && N > 8192)
         return fail(QTRAJ_EINVAL, "the vacuum evolution runs in the fused form: FP64 needs N <= 8192");
+    if (p.basis != 0 && p.basis != 1) return fail(QTRAJ_EINVAL, "basis must be 0 (analytic) or 1 (numerical)");
+    if (p.basis == 1 && !(p.alpha_s > 0)) return fail(QTRAJ_EINVAL, "the numerical basis needs alpha_s > 0");
 
     qtraj_ctx *c = new qtraj_ctx();
     c->N = N;
@@ -450,28 +470,41 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     c->dr = L / N;
     c->p = p;
     c->a0 = 2.0 / (M * (p.Nc * p.Nc - 1.0) / (2.0 * p.Nc) * p.alpha_s);
-    if (std::isfinite(c->a0)) {
-        std::vector<double> phi;
-        coulomb_u(N, c->dr, c->a0, 1, 0, phi);
-        double r1 = 0.0;
-        for (int j = 1; j < N; ++j) r1 += j * c->dr * phi[j] * phi[j];
-        c->r1s = r1 * c->dr;
-    }
     qtraj_status st = QTRAJ_OK;
     auto bail = [&](qtraj_status s) {
         qtraj_destroy(c);
         return s;
     };
+    // the overlap basis: analytic Coulomb states, or the numerical eigenstates of the grid's H
+    c->basis_host.assign((size_t)NBASIS * N, 0.0);
+    if (p.basis == 1) {
+        const int lm[3][2] = {{0, 3}, {1, 2}, {2, 1}};
+        for (const auto &q : lm) {
+            std::vector<std::vector<double>> v;
+            if ((st = numerical_states(c, q[0], q[1], v)) != QTRAJ_OK) return bail(st);
+            for (int k = 0; k < q[1]; ++k)
+                for (int b = 0; b < NBASIS; ++b)
+                    if (BASIS_L[b] == q[0] && BASIS_N[b] == q[0] + 1 + k)
+                        std::memcpy(c->basis_host.data() + (size_t)b * N, v[k].data(), sizeof(double) * N);
+        }
+    } else {
+        std::vector<double> u;
+        for (int b = 0; b < NBASIS; ++b) {
+            coulomb_u(N, c->dr, c->a0, BASIS_N[b], BASIS_L[b], u);
+            std::memcpy(c->basis_host.data() + (size_t)b * N, u.data(), sizeof(double) * N);
+        }
+    }
+    {
+        double r1 = 0.0;
+        for (int j = 1; j < N; ++j) r1 += j * c->dr * c->basis_host[j] * c->basis_host[j];
+        c->r1s = std::isfinite(r1) && r1 > 0 ? r1 * c->dr : 1.0;
+    }
     if (cudaGetDevice(&c->device) != cudaSuccess) return bail(fail(QTRAJ_ECUDA, "no CUDA device"));
     if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return bail(fail(QTRAJ_ECUDA, "cannot query the SM count"));
     st = p.precision == QTRAJ_FP32 ? build_tables<float>(c) : build_tables<double>(c);
     if (st != QTRAJ_OK) return bail(st);
-    std::vector<double> eig((size_t)NBASIS * N), u;
-    for (int s = 0; s < NBASIS; ++s) {
-        coulomb_u(N, c->dr, c->a0, BASIS_N[s], BASIS_L[s], u);
-        std::memcpy(eig.data() + (size_t)s * N, u.data(), sizeof(double) * N);
-    }
+    const std::vector<double> &eig = c->basis_host;
     if (cudaMalloc(&c->eig, sizeof(double) * eig.size()) != cudaSuccess) return bail(fail(QTRAJ_ENOMEM, "cudaMalloc"));
     if (cudaMemcpy(c->eig, eig.data(), sizeof(double) * eig.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(fail(QTRAJ_ECUDA, "upload of the Coulomb basis failed"));
@@ -528,10 +561,11 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
     const int N = c->N;
     for (int s = 0; s < n_specs; ++s) {
         const qtraj_init_spec &q = specs[s];
-        if (q.kind != 0 && q.kind != 1) return fail(QTRAJ_EINVAL, "spec %d: kind must be 0 or 1", s);
+        if (q.kind < 0 || q.kind > 2) return fail(QTRAJ_EINVAL, "spec %d: kind must be 0, 1 or 2", s);
+        if (q.kind == 2 && !(c->p.alpha_s > 0)) return fail(QTRAJ_EINVAL, "spec %d: numerical eigenstates need alpha_s > 0", s);
         if (q.l < 0 || (q.color != 0 && q.color != 1)) return fail(QTRAJ_EINVAL, "spec %d: l >= 0, color 0/1", s);
         if (q.kind == 0 && !(q.width > 0)) return fail(QTRAJ_EINVAL, "spec %d: width must be positive", s);
-        if (q.kind == 1 && (q.n < 1 || q.l >= q.n)) return fail(QTRAJ_EINVAL, "spec %d: need 0 <= l < n", s);
+        if (q.kind >= 1 && (q.n < 1 || q.l >= q.n)) return fail(QTRAJ_EINVAL, "spec %d: need 0 <= l < n", s);
     }
     std::vector<int> idx(n_traj);
     for (int t = 0; t < n_traj; ++t) {
@@ -542,18 +576,29 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
     std::vector<int> zero((size_t)n_specs * NBASIS), sl(n_specs), sc(n_specs);
     for (int s = 0; s < n_specs; ++s) {
         const qtraj_init_spec &q = specs[s];
-        if (q.kind == 1) coulomb_u(N, c->dr, c->a0, q.n, q.l, u);
-        else gauss_u(N, c->dr, q.width, q.l, u);
+        if (q.kind == 1) {
+            coulomb_u(N, c->dr, c->a0, q.n, q.l, u);
+        } else if (q.kind == 2) {
+            std::vector<std::vector<double>> v;
+            const qtraj_status st = numerical_states(c, q.l, q.n - q.l, v);
+            if (st != QTRAJ_OK) return st;
+            u = v.back();
+        } else {
+            gauss_u(N, c->dr, q.width, q.l, u);
+        }
         std::memcpy(ic.data() + (size_t)s * N, u.data(), sizeof(double) * N);
         sl[s] = q.l;
         sc[s] = q.color;
+        // an eigenstate of the basis' own kind (analytic Coulomb with the analytic basis, numerical
+        // with the numerical one) is orthogonal to the basis states of other n
+        const bool same_family = (q.kind == 1 && c->p.basis == 0) || (q.kind == 2 && c->p.basis == 1);
         for (int b = 0; b < NBASIS; ++b) {
-            const int z = q.color != 0 || q.l != BASIS_L[b] || (q.kind == 1 && q.n != BASIS_N[b]);
+            const int z = q.color != 0 || q.l != BASIS_L[b] || (same_family && q.n != BASIS_N[b]);
             zero[(size_t)s * NBASIS + b] = z;
             double o = 0.0;
             if (!z) {
-                coulomb_u(N, c->dr, c->a0, BASIS_N[b], BASIS_L[b], phi);
-                for (int j = 1; j < N; ++j) o += phi[j] * u[j];
+                const double *ph = c->basis_host.data() + (size_t)b * N;
+                for (int j = 1; j < N; ++j) o += ph[j] * u[j];
                 o *= c->dr;
             }
             ov0[((size_t)s * NBASIS + b) * 2] = o;
@@ -632,6 +677,14 @@ qtraj_status qtraj_set_trace(qtraj_ctx *c, int every, int n_traced, int max_reco
     c->trace_cap = every > 0 ? max_records : 0;
     c->trace = every > 0 ? d_records : nullptr;
     c->trace_cnt = every > 0 ? d_counts : nullptr;
+    return QTRAJ_OK;
+}
+
+qtraj_status qtraj_basis_get(const qtraj_ctx *c, double *out)
+{
+    g_err.clear();
+    if (!c || !out) return fail(QTRAJ_EINVAL, "null argument");
+    std::memcpy(out, c->basis_host.data(), sizeof(double) * c->basis_host.size());
     return QTRAJ_OK;
 }
 

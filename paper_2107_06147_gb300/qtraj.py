@@ -31,7 +31,8 @@ class QtrajError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int), ("max_jumps", C.c_int),
                 ("r_max", C.c_double), ("l_cap", C.c_int), ("use_rmin", C.c_int), ("precision", C.c_int),
-                ("form", C.c_int), ("save_states", C.c_int), ("variant", C.c_int), ("t_vacuum", C.c_double)]
+                ("form", C.c_int), ("save_states", C.c_int), ("variant", C.c_int), ("t_vacuum", C.c_double),
+                ("basis", C.c_int)]
 
 
 class InitSpec(C.Structure):
@@ -90,6 +91,7 @@ _PROTOS = {
     "qtraj_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.POINTER(InitSpec), C.c_int,
                              C.POINTER(C.c_int)]),
     "qtraj_set_spec_idx": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int]),
+    "qtraj_basis_get": (C.c_int, [C.c_void_p, C.c_void_p]),
     "qtraj_set_trace": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_set_profiles": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
     "qtraj_evolve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Medium), C.c_int, C.POINTER(C.c_int),
@@ -159,14 +161,16 @@ class Config:
     save_states: int = 0
     variant: int = 0
     t_vacuum: float = 0.0
+    basis: int = 0
 
     def params(self) -> Params:
         return Params(self.alpha_s, self.Nc, self.deriv_type, self.max_jumps, self.r_max, self.l_cap, self.use_rmin,
-                      self.precision, self.form, self.save_states, self.variant, self.t_vacuum)
+                      self.precision, self.form, self.save_states, self.variant, self.t_vacuum, self.basis)
 
 
 def init_spec(kind="gauss", width=0.2, n=1, l=0, color=0) -> InitSpec:
-    return InitSpec(0 if kind == "gauss" else 1, width, n, l, color)
+    """kind 'gauss', 'coulomb' (analytic eigenstate) or 'numerical' (eigenstate of the grid's H)."""
+    return InitSpec({"gauss": 0, "coulomb": 1, "numerical": 2}[kind], width, n, l, color)
 
 
 def medium(T0=0.425, tau0=0.6, Tf=0.25, kappa_hat=5.0, gamma_hat=0.0) -> Medium:
@@ -225,6 +229,12 @@ class Engine:
             idx = self._spec_idx.ctypes.data_as(C.POINTER(C.c_int))
         _check(self.lib.qtraj_init(self.ctx, C.c_void_p(ptr), have, n_traj, arr, len(specs), idx), self.ctx)
         self.n_traj = n_traj
+
+    def basis(self) -> np.ndarray:
+        """The overlap basis, (NBASIS, N) in the order of the survival ratios."""
+        out = np.zeros((NBASIS, self.cfg.N))
+        _check(self.lib.qtraj_basis_get(self.ctx, C.c_void_p(out.ctypes.data)), self.ctx)
+        return out
 
     def set_trace(self, every: int, n_traced: int = 1, max_records: int = 1024):
         """Per-step summary rows for the first n_traced trajectories of later evolves (every = 0: off).

@@ -357,6 +357,53 @@ def test_trace_needs_fused_form(q):
     e.close()
 
 
+@pytest.mark.parametrize("form,precision", [(0, 0), (1, 0), (0, 1)])
+def test_numerical_basis(q, form, precision):
+    """Numerical vacuum eigenstates (initType 100 / ProjType 1): the library's eigensolver gives the
+    dense eigenvectors of the grid's Hamiltonian, and trajectories started from Gaussian, analytic
+    and numerical eigenstates, measured in the numerical basis, follow the oracle run with the same
+    basis.  The two eigensolvers agree to ~1e-10, so the FP64 survival ratios get 1e-8."""
+    import torch
+    import oracle as o
+    from oracle import eigen
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=512, n_traj=18, seed=61)
+    w.grid.L = 20.0
+    w.inits = [inputs.InitSpec("gauss", 0.3, 1, 0, 0), inputs.InitSpec("coulomb", 0.0, 2, 0, 0),
+               inputs.InitSpec("numerical", 0.0, 1, 0, 0), inputs.InitSpec("numerical", 0.0, 2, 1, 0),
+               inputs.InitSpec("numerical", 0.0, 3, 0, 1)]
+    w.init_idx = (np.arange(18) % 5).astype(np.int32)
+    g, _, media = oracle_inputs(w)
+    g.basis = eigen.numerical_basis(g)
+    e = q.Engine(q.Config(N=512, L=20.0, dt=w.grid.dt, precision=precision, form=form, save_states=1, basis=1))
+    nb = e.basis()
+    assert np.abs(nb - g.basis).max() < 1e-9 * np.abs(g.basis).max()
+    inits = []
+    for s in w.inits:
+        if s.kind == "numerical":
+            _, v = eigen.vacuum_eigenstates(g, s.l, s.n - s.l)
+            inits.append(o.given_state(v[-1], s.n, s.l, s.color))
+        else:
+            inits.append(o.init_spec(s.kind, s.width, s.n, s.l, s.color))
+    ref, _, uref = o.run_batch(g, inits, w.init_idx, media, w.medium_idx, w.seeds, want_states=True)
+    e.init([q.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits], 18, w.init_idx)
+    e.evolve([q.medium(m.T0, m.tau0, m.Tf, m.kappa_hat, m.gamma_hat) for m in w.media], w.seeds, w.medium_idx)
+    obs = e.observables()
+    u = e.states()
+    torch.cuda.synchronize()
+    e.close()
+    if precision == 0:
+        ok = ((obs["flags"] | ref["flags"]) & q.F_BORDERLINE) == 0
+        for f in ("n_jumps", "first_jump_step", "l", "color", "n_steps_exec", "flags"):
+            assert np.array_equal(obs[f][ok], ref[f][ok]), f
+        np.testing.assert_allclose(obs["surv"][ok], ref["surv"][ok], rtol=1e-8, atol=1e-14)
+        ran = ok & (ref["n_steps_exec"] > 0)
+        du = np.linalg.norm(u[ran] - uref[ran], axis=1) / np.linalg.norm(uref[ran], axis=1)
+        assert du.max() < 1e-9, du.max()
+    else:
+        check_fp32(q, obs, ref, u, uref)
+
+
 def test_static_entry_rejects_vacuum_evolution(q):
     import ctypes as C
     import torch
