@@ -99,7 +99,7 @@ struct qtraj_ctx {
     qtraj_params p{};
     int device = 0, sm_count = 0;
     // read-only tables
-    void *W = nullptr, *KT = nullptr, *sinpre = nullptr, *statV = nullptr, *statV2 = nullptr;
+    void *W = nullptr, *WL = nullptr, *KT = nullptr, *sinpre = nullptr, *statV = nullptr, *statV2 = nullptr;
     double *eig = nullptr;
     double *ic = nullptr, *ov0 = nullptr;
     int *ov0_zero = nullptr, *spec_l = nullptr, *spec_color = nullptr;
@@ -198,6 +198,17 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
                 stat[((size_t)col * LTAB + l) * N + j] = v;
                 stat2[((size_t)col * LTAB + l) * N + j] = v2;
             }
+    // last-pass twiddles of the fused kernel, W^(m g) for m < R, g < G = N/(2R), one compact section
+    // [R][G] (N/2 entries) per radix R = 16, 8, 4 at offsets 0, N/2, N: a kernel reads the section of
+    // its own radix, and the threads of a warp read consecutive entries
+    std::vector<PC> WL((size_t)3 * (N / 2));
+    for (int sec = 0; sec < 3; ++sec) {
+        const int R = 16 >> sec, G = N / (2 * R);
+        for (int m = 0; m < R; ++m)
+            for (int g = 0; g < G; ++g) WL[(size_t)sec * (N / 2) + (size_t)m * G + g] = W[(size_t)m * g];
+    }
+    CK(cudaMalloc(&c->WL, sizeof(PC) * WL.size()));
+    CK(cudaMemcpy(c->WL, WL.data(), sizeof(PC) * WL.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->W, sizeof(PC) * N));
     CK(cudaMalloc(&c->KT, sizeof(PC) * N));
     CK(cudaMalloc(&c->sinpre, sizeof(PR) * N));
@@ -216,6 +227,7 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     Tables<T> t;
     using PC = typename Prec<T>::C;
     t.W = (const PC *)c->W;
+    t.WL = (const PC *)c->WL;
     t.KT = (const PC *)c->KT;
     t.sinpre = (const typename Prec<T>::Rl *)c->sinpre;
     t.statV = (const PC *)c->statV;
@@ -521,6 +533,7 @@ void qtraj_destroy(qtraj_ctx *c)
     if (!c) return;
     cudaDeviceSynchronize();
     free_ptr(c->W);
+    free_ptr(c->WL);
     free_ptr(c->KT);
     free_ptr(c->sinpre);
     free_ptr(c->statV);

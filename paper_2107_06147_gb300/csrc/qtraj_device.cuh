@@ -326,6 +326,7 @@ static_assert(sizeof(qtraj_trace_rec) == 80, "qtraj_trace_rec layout");
 template <typename T> struct Tables {
     using C = typename Prec<T>::C;
     const C *W;                        // N twiddles exp(-2 pi i t / N)
+    const C *WL;                       // last-pass twiddles W^(m g): sections [R][N/(2R)] for R = 16, 8, 4
     const C *KT;                       // N kinetic factors exp(-i T_kin(p_k) dt) * 2/N, k = 0..N-1
     const typename Prec<T>::Rl *sinpre; // N values sin(pi j / N)
     const C *statV;                    // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
