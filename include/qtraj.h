@@ -228,6 +228,12 @@ typedef struct {
 } qtraj_kernel_info;
 qtraj_status qtraj_kernel_info_get(const qtraj_ctx *ctx, qtraj_kernel_info *out);
 
+/* Measurement (the paper has no counterpart): the FMA throughput of the current device in
+ * TFLOP/s (2 flops per fused multiply-add), precision QTRAJ_FP32 or QTRAJ_FP64 -- every thread runs 8
+ * independent FMA chains, 8 blocks of 256 threads per SM, best of 3 timed launches after a warm-up.
+ * The achievable denominator of a roofline for ALU-bound kernels.  Synchronous; allocates 8 bytes. */
+qtraj_status qtraj_fma_peak(int precision, double *tflops);
+
 /* ---------------------------------------------------------------------------------------------
  * Serving: continuous batching of trajectory requests.  (The paper has no counterpart: its program
  * evolves one batch per invocation.)

@@ -92,6 +92,7 @@ _PROTOS = {
                              C.POINTER(C.c_int)]),
     "qtraj_set_spec_idx": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int]),
     "qtraj_basis_get": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "qtraj_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "qtraj_set_trace": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_set_profiles": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
     "qtraj_evolve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Medium), C.c_int, C.POINTER(C.c_int),
@@ -166,6 +167,13 @@ class Config:
     def params(self) -> Params:
         return Params(self.alpha_s, self.Nc, self.deriv_type, self.max_jumps, self.r_max, self.l_cap, self.use_rmin,
                       self.precision, self.form, self.save_states, self.variant, self.t_vacuum, self.basis)
+
+
+def fma_peak(precision=FP32) -> float:
+    """Measured FMA throughput of the current device, TFLOP/s."""
+    v = C.c_double()
+    _check(load().qtraj_fma_peak(precision, C.byref(v)))
+    return v.value
 
 
 def init_spec(kind="gauss", width=0.2, n=1, l=0, color=0) -> InitSpec:

@@ -404,6 +404,18 @@ def test_numerical_basis(q, form, precision):
         check_fp32(q, obs, ref, u, uref)
 
 
+def test_fma_peak_measurement(q):
+    """The FMA microbenchmark: FP32 within (0.5, 1.1] of the unit-count peak (SMs x 128 lanes x 2
+    flops at the maximum SM clock), FP64 far below it (GB300's narrow FP64 pipe)."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    f32 = q.fma_peak(q.FP32)
+    f64 = q.fma_peak(q.FP64)
+    assert 0.5 * nominal < f32 <= 1.1 * nominal, (f32, nominal)
+    assert 0 < f64 < 0.25 * f32, (f64, f32)
+
+
 def test_static_entry_rejects_vacuum_evolution(q):
     import ctypes as C
     import torch
