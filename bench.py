@@ -248,20 +248,24 @@ def run_ours(args):
               "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
               "config": workload_config(B) | {"parallelism": f"replicas x{world} (disjoint trajectory ids)"},
               "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
-                      "h2d_bytes_per_step": int(B * 24 + 18 * 24 + 6 * 64),
+                      # staged per evolve: a 24-byte record per trajectory and per (state, medium)
+                      # group (18), a 104-byte record per medium (6)
+                      "h2d_bytes_per_step": int(B * 24 + 18 * 24 + 6 * 104),
                       "d2h_bytes_per_step": int(B * qtraj.OBS_DTYPE.itemsize + 4)},
               "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
               "kernel": {"threads_per_traj": kinfo.threads_per_traj, "ctas_per_sm": kinfo.ctas_per_sm,
                          "smem_bytes": kinfo.smem_bytes, "regs": kinfo.regs_per_thread, "radix": kinfo.radix,
                          "variant": args.variant}}
 
-    if rank == 0 and not args.no_compare:
+    # the comparison forms, the CPU baseline and serving are single-GPU measurements: with N > 1 they
+    # would hold every GPU at the final barrier, so they run at N = 1 only
+    if rank == 0 and world == 1 and not args.no_compare:
         result["plain_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.PLAIN, args.compare_batch)
         result["fused_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.FUSED, args.compare_batch)
         result["speedup_vs_plain_fp64"] = round(value / world / result["plain_fp64"]["value"], 2)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and world == 1 and not args.no_serving:
         eng.close()
         result["serving"] = run_serving(args)
     if world > 1:

@@ -174,6 +174,17 @@ def test_options(q, opt, form):
     check_fp64(q, obs, ref, u, uref)
 
 
+@pytest.mark.parametrize("opt", [dict(r_max=0.6), dict(max_jumps=1), dict(l_cap=1), dict(use_rmin=0),
+                                 dict(deriv_type=1)])
+def test_options_fp32(q, opt):
+    """The options in the fused FP32 form against the FP64 oracle (FP32 criteria)."""
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=64, n_traj=32, seed=5)
+    ref, uref = run_oracle(w, **opt)
+    obs, u = run_gpu(q, w, q.FP32, **opt)
+    check_fp32(q, obs, ref, u, uref)
+
+
 @pytest.mark.parametrize("opt", [dict(max_jumps=0), dict(max_jumps=1), dict(max_jumps=2), dict(l_cap=0),
                                  dict(l_cap=1), dict(l_cap=2)])
 @pytest.mark.parametrize("precision", [0, 1])
