@@ -277,6 +277,40 @@ def run_ours(args):
         print(json.dumps(result))
 
 
+def run_uneven(args):
+    """Throughput of the uneven-batch workload: --uneven trajectories with N drawn from
+    {1024, 2048, 4096, 8192} (L = N * 5/512), l0 in {0, 1, 2} (Gaussian singlets of width 0.2),
+    T0 ~ U[0.30, 0.60] GeV from tau0 = 0.6 fm/c to 0.25 GeV, kappa_hat ~ U[3, 7], gamma_hat ~ U[-3.5, 0],
+    seeds = ids (PCG64 seed 0), all grid sizes launched together on concurrent streams (batching.py).
+    Every trajectory has its own medium, so the rMin shortcut (one no-jump run per (state, medium)
+    group) would double the work: it is off.  One JSON line."""
+    import torch
+
+    from paper_2107_06147_gb300 import batching, inputs, qtraj
+    u = inputs.uneven(n_traj=args.uneven, seed=0)
+    inits = [qtraj.init_spec("gauss", 0.2, 1 + int(l), int(l), 0) for l in u["l0"]]
+    media = [qtraj.medium(float(u["T0"][i]), 0.6, 0.25, float(u["kappa_hat"][i]), float(u["gamma_hat"][i]))
+             for i in range(args.uneven)]
+    prec = qtraj.FP32 if args.precision == "fp32" else qtraj.FP64
+    w = batching.UnevenBatch(u["N"][:64], inits[:64], media[:64], precision=prec, use_rmin=0)
+    w.run(u["seeds"][:64])   # loads every kernel instantiation before the timed run
+    w.close()
+    b = batching.UnevenBatch(u["N"], inits, media, precision=prec, use_rmin=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    obs = b.run(u["seeds"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = b.stats()
+    b.close()
+    steps = int(obs["n_steps_exec"].sum())
+    per_n = {int(N): {"trajectories": int(s.n_traj), "traj_steps": int(s.steps_executed), "kernel_ms": round(s.ms_main, 1)}
+             for N, s in st.items()}
+    print(json.dumps({"uneven": True, "trajectories": args.uneven, "precision": args.precision, "traj_steps": steps,
+                      "wall_s": round(wall, 2), "traj_steps_per_s": round(steps / wall, 1), "per_N": per_n,
+                      "jumps_mean": round(float(obs["n_jumps"].mean()), 2)}))
+
+
 def run_serving_sweep(args):
     """The first --serving-requests requests of the stream replayed at each offered rate of
     --serving-sweep (the arrival gaps of the 200 req/s stream rescaled): latency against offered load,
@@ -455,12 +489,19 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
     ap.add_argument("--profile-steps", type=int, default=1000)
+    ap.add_argument("--uneven", type=int, default=0, metavar="NTRAJ",
+                    help="throughput of the uneven-batch workload (NTRAJ trajectories of mixed N, l, lifetime)")
     ap.add_argument("--serving-sweep", default="", metavar="RATES",
                     help="comma-separated offered rates (req/s): replay the --serving-requests prefix at each")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NTRAJ",
                     help="paired FP64/FP32 study on NTRAJ trajectories of N=8192, L=80, dt=0.0005 (no timing line)")
     args = ap.parse_args()
     args.batch_given = any(a.startswith("--batch") for a in sys.argv[1:])
+    if args.uneven:
+        from paper_2107_06147_gb300 import build
+        build.build()
+        run_uneven(args)
+        return
     if args.serving_sweep:
         from paper_2107_06147_gb300 import build
         build.build()
