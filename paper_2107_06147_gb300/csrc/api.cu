@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libqtraj (include/qtraj.h): context, read-only tables, workspace layout,
 // and the orchestration of an evolve (no-jump runs of every (initial state, medium) group first,
 // then all trajectories).  All host-side tables are built in FP64.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -163,12 +164,36 @@ Layout layout(const qtraj_ctx *c, int n)
     return L;
 }
 
+// the static part of the space kernel for every (colour, l < LTAB, j), rows [colour][l][j]:
+// exp(-i V dt/2) (s1) and exp(-i V dt) (s2), V = coul_c / r + l(l+1) / (M r^2) at r = j dr, in FP64
+// (entry j = 0 is zero: u(0) = 0).  Built on the device: 2 x 2 x LTAB x N phases.
+template <typename T>
+__global__ void stat_rows(typename Prec<T>::C *s1, typename Prec<T>::C *s2, int N, double dr, double M, double dt,
+                          double coul0, double coul1)
+{
+    const size_t n = (size_t)2 * LTAB * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % (size_t)N), row = (int)(i / (size_t)N);
+        const int col = row / LTAB, l = row % LTAB;
+        double c1 = 0.0, sn1 = 0.0, c2 = 0.0, sn2 = 0.0;
+        if (j > 0) {
+            const double r = j * dr;
+            const double V = (col ? coul1 : coul0) / r + (double)l * (l + 1) / (M * r * r);
+            const double ph = -V * dt * 0.5;
+            sincos(ph, &sn1, &c1);
+            sincos(2.0 * ph, &sn2, &c2);
+        }
+        s1[i] = Prec<T>::from_double(c1, sn1);
+        s2[i] = Prec<T>::from_double(c2, sn2);
+    }
+}
+
 template <typename T> qtraj_status build_tables(qtraj_ctx *c)
 {
     using PC = typename Prec<T>::C;
     using PR = typename Prec<T>::Rl;
     const int N = c->N;
-    std::vector<PC> W(N), KT(N), stat((size_t)2 * LTAB * N), stat2((size_t)2 * LTAB * N);
+    std::vector<PC> W(N), KT(N);
     std::vector<PR> sp(N);
     for (int t = 0; t < N; ++t) {
         const double a = -2.0 * PI * (double)t / N;
@@ -184,20 +209,6 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
     }
     const double Nc = c->p.Nc, CF = (Nc * Nc - 1.0) / (2.0 * Nc);
     const double coul[2] = {-CF * c->p.alpha_s, c->p.alpha_s / (2.0 * Nc)};
-    for (int col = 0; col < 2; ++col)
-        for (int l = 0; l < LTAB; ++l)
-            for (int j = 0; j < N; ++j) {
-                PC v = Prec<T>::make(0.0, 0.0), v2 = v;
-                if (j > 0) {
-                    const double r = j * c->dr;
-                    const double V = coul[col] / r + (double)l * (l + 1) / (c->M * r * r);
-                    const double ph = -V * c->dt * 0.5;
-                    v = Prec<T>::make(std::cos(ph), std::sin(ph));
-                    v2 = Prec<T>::make(std::cos(2.0 * ph), std::sin(2.0 * ph));
-                }
-                stat[((size_t)col * LTAB + l) * N + j] = v;
-                stat2[((size_t)col * LTAB + l) * N + j] = v2;
-            }
     // last-pass twiddles of the fused kernel, W^(m g) for m < R, g < G = N/(2R), one compact section
     // [R][G] (N/2 entries) per radix R = 16, 8, 4 at offsets 0, N/2, N: a kernel reads the section of
     // its own radix, and the threads of a warp read consecutive entries
@@ -212,13 +223,22 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
     CK(cudaMalloc(&c->W, sizeof(PC) * N));
     CK(cudaMalloc(&c->KT, sizeof(PC) * N));
     CK(cudaMalloc(&c->sinpre, sizeof(PR) * N));
-    CK(cudaMalloc(&c->statV, sizeof(PC) * stat.size()));
-    CK(cudaMalloc(&c->statV2, sizeof(PC) * stat2.size()));
-    CK(cudaMemcpy(c->statV2, stat2.data(), sizeof(PC) * stat2.size(), cudaMemcpyHostToDevice));
+    const size_t nstat = (size_t)2 * LTAB * N;
+    CK(cudaMalloc(&c->statV, sizeof(PC) * nstat));
+    CK(cudaMalloc(&c->statV2, sizeof(PC) * nstat));
     CK(cudaMemcpy(c->W, W.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->KT, KT.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->sinpre, sp.data(), sizeof(PR) * N, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->statV, stat.data(), sizeof(PC) * stat.size(), cudaMemcpyHostToDevice));
+    // a private non-blocking stream: building a context waits for nothing else on the device
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    const int blocks = (int)std::min<size_t>((nstat + 255) / 256, 4096);
+    stat_rows<T><<<blocks, 256, 0, s>>>((PC *)c->statV, (PC *)c->statV2, N, c->dr, c->M, c->dt, coul[0], coul[1]);
+    cudaError_t e = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+    cudaStreamDestroy(s);
+    CK(e);
     return QTRAJ_OK;
 }
 

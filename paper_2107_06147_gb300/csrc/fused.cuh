@@ -298,8 +298,8 @@ template <> struct Dyn<double> {
 __device__ __forceinline__ void k_sincospi(float y, float *s, float *c) { sincospif(y, s, c); }
 __device__ __forceinline__ void k_sincospi(double y, double *s, double *c) { sincospi(y, s, c); }
 
-// static factor of a (colour, l) row beyond the table, evaluated in FP64 (rare: l grows by one per
-// jump); span 1 = half step, 2 = full step
+// static factor of a (colour, l) row beyond the table (l >= LTAB, some 33,000 jumps from l = 0),
+// evaluated in FP64; span 1 = half step, 2 = full step
 template <typename T>
 __device__ __noinline__ typename Prec<T>::C static_far(double coul, double M, double dt, int l, double r, double span)
 {

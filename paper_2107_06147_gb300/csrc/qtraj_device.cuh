@@ -9,7 +9,7 @@
 namespace qt {
 
 constexpr int NBASIS = QTRAJ_NBASIS;
-constexpr int LTAB = 64;             // (colour, l) rows of the static space-kernel table
+constexpr int LTAB = 256;            // l rows per colour of the static space-kernel tables
 constexpr double BORDER_EPS = 1e-12; // |norm^2 - r| below this flags a borderline comparison
 
 // ------------------------------------------------------------------------------------------------
@@ -364,7 +364,8 @@ struct LaunchArgs {
 };
 
 // static part of the half-step space kernel for (colour, l, j); rows beyond the table are
-// evaluated in FP64 on the fly (rare: l grows by one per jump)
+// evaluated in FP64 on the fly.  A jump moves l by one, and l(l+1) grows by 2 per jump on average
+// (l -> l+1 with probability (l+1)/(2l+1)), so l >= 256 takes some 33,000 jumps.
 template <typename T>
 __device__ __forceinline__ typename Prec<T>::C static_factor(const Tables<T> &tb, int N, int c, int l, int j)
 {

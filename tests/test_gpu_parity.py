@@ -562,6 +562,28 @@ def test_uneven_batch_against_oracle(q, precision):
         assert np.abs(obs["surv"].mean(0) - ref["surv"].mean(0)).max() <= FP32_ENSEMBLE_ABS
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_high_l_table_edge(q, precision):
+    """Angular momenta at the edge of the static-factor table (rows l < 256 are tabulated, larger l
+    evaluated on the fly) and beyond it: singlet and octet Gaussians r^{l+1} e^{-r^2/(2 0.2^2)}
+    (peak near r = 3.3) with l = 254 .. 257 and 300 on N = 1024, L = 10, in media strong enough
+    that jumps carry l back and forth across 255/256."""
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=1024, n_traj=24, seed=21)
+    w.grid.L = 10.0
+    w.inits = [inputs.InitSpec("gauss", 0.2, 1, l, c)
+               for l, c in ((254, 0), (255, 1), (256, 0), (257, 1), (255, 0), (300, 1))]
+    ref, uref = run_oracle(w)
+    assert (ref["n_jumps"] >= 3).mean() > 0.5
+    crossed = [(i, l) for i, l in zip(w.init_idx, ref["l"]) if (w.inits[i].l < 256) != (l < 256)]
+    assert len(crossed) >= 3, crossed
+    obs, u = run_gpu(q, w, precision)
+    if precision == 0:
+        check_fp64(q, obs, ref, u, uref)
+    else:
+        check_fp32(q, obs, ref, u, uref, min_same=0.8)
+
+
 def test_precision_study_small(q):
     """The paired FP64/FP32 study (precision.run) on a small grid: 256 trajectories of the 1S Gaussian
     through the whole Bjorken medium (11,899 steps).  FP32 keeps most jump sequences and its ensemble
