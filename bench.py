@@ -319,7 +319,7 @@ def run_serving_sweep(args):
 
     from paper_2107_06147_gb300 import inputs, serving
     for rate in [float(r) for r in args.serving_sweep.split(",")]:
-        st = inputs.serving_stream(n_requests=args.serving_requests, rate_hz=200.0, seed=1)
+        st = inputs.serving_prefix(args.serving_requests)
         arrival = st["arrival_s"] * (200.0 / rate)
         reqs = serving.requests_from_stream(st)
         Ns = sorted(set(int(n) for n in st["N"]))
@@ -345,7 +345,7 @@ def run_serving(args):
     import torch
 
     from paper_2107_06147_gb300 import inputs, serving
-    st = inputs.serving_stream(n_requests=args.serving_requests, rate_hz=200.0, seed=1)
+    st = inputs.serving_prefix(args.serving_requests)
     reqs = serving.requests_from_stream(st)
     Ns = sorted(set(int(n) for n in st["N"]))
     srv = serving.Server(Ns=tuple(Ns), slots_per_n=2, wave_mult=4)

@@ -175,3 +175,11 @@ def serving_stream(n_requests: int = 256, rate_hz: float = 200.0, seed: int = 1,
     N = rng.choice(np.array(N_choices), n_requests)
     return {"arrival_s": arrival, "init": init, "kappa_hat": kap, "gamma_hat": gam, "T0": T0,
             "ntraj": ntraj, "N": N}
+
+
+def serving_prefix(n: int, rate_hz: float = 200.0, seed: int = 1) -> dict:
+    """The first n requests of the 256-request serving stream.  (serving_stream draws each field for
+    all requests in turn, so a stream generated with n_requests = n is a different set of requests,
+    not a prefix.)"""
+    st = serving_stream(n_requests=max(256, n), rate_hz=rate_hz, seed=seed)
+    return {k: v[:n] for k, v in st.items()}
