@@ -40,7 +40,7 @@ METRIC = "traj-steps/s at N=4096 vs plain FP64 GPU form at stated error; p99 req
 UNIT = "traj-steps/s"
 N_GRID, L_BOX, DT = 4096, 40.0, 0.001
 # DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture
-PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 26.24
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 7.72
 N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
