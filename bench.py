@@ -39,8 +39,9 @@ sys.path.insert(0, ROOT)
 METRIC = "traj-steps/s at N=4096 vs plain FP64 GPU form at stated error; p99 request latency"
 UNIT = "traj-steps/s"
 N_GRID, L_BOX, DT = 4096, 40.0, 0.001
-# DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture
-PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 7.72
+# DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture of the current
+# kernel source (None until the kernel has been captured again after a change)
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = None
 N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
@@ -231,7 +232,7 @@ def run_ours(args):
     # (dram__bytes_read.sum + dram__bytes_write.sum over 456 trajectories x 1000 steps) scaled to the
     # launch's trajectory-steps
     traffic = None
-    if args.precision == "fp32" and args.variant == 0:
+    if args.precision == "fp32" and args.variant == 0 and PROFILED_DRAM_BYTES_PER_TRAJ_STEP is not None:
         traffic = round(PROFILED_DRAM_BYTES_PER_TRAJ_STEP * main_steps / args.steps)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,

@@ -56,9 +56,9 @@ template <int N, int V = 0> struct FusedPlan {
 
 
 // ------------------------------------------------------------------------------------------------
-// accumulators: FP32 forms accumulate sums of squares in double-float (error-free transformations
-// in FP32), so norms carry FP64-level accuracy without GB300's narrow FP64 pipe in the step loop;
-// FP64 forms accumulate in double.
+// accumulators: FP32 forms accumulate sums of squares with compensated (cascaded) summation and
+// combine partial sums in double-float (error-free transformations in FP32), so no FP64 instruction
+// enters the step loop (GB300's FP64 pipe is narrow); FP64 forms accumulate in double.
 // ------------------------------------------------------------------------------------------------
 struct DF { float hi, lo; };
 
@@ -76,26 +76,19 @@ __device__ __forceinline__ DF df_add(DF a, DF b)
     const float hi = s.hi + t;
     return {hi, t - (hi - s.hi)};
 }
-__device__ __forceinline__ DF df_add_f(DF a, float p, float e)   // a + (p + e)
-{
-    DF s = two_sum(a.hi, p);
-    const float t = s.lo + (a.lo + e);
-    const float hi = s.hi + t;
-    return {hi, t - (hi - s.hi)};
-}
 
 template <typename T> struct SqAcc;
 template <> struct SqAcc<float> {
     DF v{0.f, 0.f};
-    // v += w |a|^2, the squares and the product with w split exactly
+    // v += w |a|^2: the term is rounded once (a relative error of ~1e-7, independent from term to
+    // term and unbiased), the running sum is compensated (the TwoSum errors collect in v.lo), so a
+    // sum of n terms is good to ~1e-7 / sqrt(n) relative, far below the FP32 state's own rounding
+    // noise (~1e-6 per step); the waiting-time comparison needs no more
     __device__ __forceinline__ void add_w(cpx<float> a, float w)
     {
-        const float px = a.x * a.x, ex = fmaf(a.x, a.x, -px);
-        const float py = a.y * a.y, ey = fmaf(a.y, a.y, -py);
-        const DF s = two_sum(px, py);
-        const float sl = s.lo + ex + ey;
-        const float p = s.hi * w, ep = fmaf(s.hi, w, -p) + sl * w;
-        v = df_add_f(v, p, ep);
+        const float q = w * fmaf(a.x, a.x, a.y * a.y);
+        const DF t = two_sum(v.hi, q);
+        v = DF{t.hi, v.lo + t.lo};
     }
     __device__ __forceinline__ void shfl_add(unsigned mask, int off, int w)
     {
