@@ -352,12 +352,16 @@ template <typename T, int N, int V> struct Fused {
     using DR = DFTI<T, R>;
 
     static __device__ __forceinline__ int pad(int j) { return j + j / R; }
+    // E/odd layout of the transform's output (and of the state between transforms): S_{2k} at
+    // even_pos(k), S_{2k+1} at odd_pos(k).  (An XOR swizzle of both areas, meant to spread the
+    // even/odd lanes of the transform's load over all banks, measured 0.4-4.6% slower.)
+    static __device__ __forceinline__ int even_pos(int k) { return k; }
     static __device__ __forceinline__ int odd_pos(int k) { return N / 2 + k + k / R; }
     static __device__ __forceinline__ int b_of(int g, int t) { return t == 0 ? (g == 0 ? 0 : g) : (g == 0 ? NR / 2 : NR - g); }
     // global index of register element e (first/last-pass layout)
     static __device__ __forceinline__ int idx(int g, int e) { return b_of(g, e / R) + (e % R) * NR; }
     // shared-memory position of S_j in the E/odd layout
-    static __device__ __forceinline__ int s_pos(int j) { return (j & 1) ? odd_pos(j >> 1) : (j >> 1); }
+    static __device__ __forceinline__ int s_pos(int j) { return (j & 1) ? odd_pos(j >> 1) : even_pos(j >> 1); }
 
     // y_j = s (f_j + f_{N-j}) + (f_j - f_{N-j})/2 for the pair (ea, eb) = (j, N-j)
     static __device__ __forceinline__ void pre_pair(cpx<T> *x, int ea, int eb, RL s)
@@ -386,7 +390,7 @@ template <typename T, int N, int V> struct Fused {
     // E_k = (i/2)(Y_k - Y_{N-k}) -> [k];  C_k = (Y_k + Y_{N-k})/2 (C_0 halved) -> odd area
     static __device__ __forceinline__ void post_pair(cpx<T> *buf, int k, cpx<T> A, cpx<T> B)
     {
-        buf[k] = mul_i(scale(A - B, (T)0.5));
+        buf[even_pos(k)] = mul_i(scale(A - B, (T)0.5));
         buf[odd_pos(k)] = scale(A + B, (T)0.5);
     }
 
@@ -402,7 +406,7 @@ template <typename T, int N, int V> struct Fused {
                 else post_pair(buf, (NR - g) + (R - 1 - m) * NR, Y(x, 1, R - 1 - m), Y(x, 0, m));
             }
         } else {
-            buf[0] = mk<T>(0, 0);
+            buf[even_pos(0)] = mk<T>(0, 0);
             buf[odd_pos(0)] = scale(Y(x, 0, 0), (T)0.5);      // S_1 = C_0 / 2 = Y_0 / 2
 #pragma unroll
             for (int m = 1; m < R / 2; ++m) post_pair(buf, m * NR, Y(x, 0, m), Y(x, 0, R - m));
@@ -418,10 +422,9 @@ template <typename T, int N, int V> struct Fused {
     {
         constexpr int W = G < 32 ? G : 32;
         const unsigned mask = lane_mask<G>();
-        cpx<T> *p = buf + odd_pos(g * R);
         cpx<T> v[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = p[q];
+        for (int q = 0; q < R; ++q) v[q] = buf[odd_pos(g * R + q)];
         Carry<T> tot;
 #pragma unroll
         for (int q = 0; q < R; ++q) tot.add(v[q]);
@@ -445,7 +448,7 @@ template <typename T, int N, int V> struct Fused {
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             run = run + v[q];
-            p[q] = excl.plus(run);
+            buf[odd_pos(g * R + q)] = excl.plus(run);
         }
     }
 
@@ -546,7 +549,7 @@ template <typename T, int N, int V> struct Fused {
 
 // ------------------------------------------------------------------------------------------------
 // pointwise work on the E/odd layout: thread g visits k = g, g + G, ... < N/2 and the two elements
-// S_{2k} (at [k]) and S_{2k+1} (at odd_pos(k))
+// S_{2k} (at even_pos(k) = k) and S_{2k+1} (at odd_pos(k))
 // ------------------------------------------------------------------------------------------------
 template <typename T, int N, int V> struct Pointwise {
     using K = Fused<T, N, V>;
@@ -578,7 +581,7 @@ template <typename T, int N, int V> struct Pointwise {
 #pragma unroll
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
-                const int p = par ? K::odd_pos(k) : k;
+                const int p = par ? K::odd_pos(k) : K::even_pos(k);
                 const T fj = (T)j;
                 // the dynamic factor exp(a) exp(i pi y) is close to 1 and changes little from step to
                 // step; it is applied as w + w f1 with f1 its deviation from 1, evaluated so that the
@@ -625,7 +628,7 @@ template <typename T, int N, int V> struct Pointwise {
         for (int k = g; k < N / 2; k += G) {
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
-                const int p = par ? K::odd_pos(k) : k;
+                const int p = par ? K::odd_pos(k) : K::even_pos(k);
                 const T fj = (T)j, j2 = fj * fj;
                 cpx<T> v = buf[p];
                 if (after_last) {
@@ -665,7 +668,7 @@ template <typename T, int N, int V> struct Pointwise {
         for (int k = g; k < N / 2; k += G)
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
-                const cpx<double> e = end_value(buf, tb, c, l, j, par ? K::odd_pos(k) : k, A, B);
+                const cpx<double> e = end_value(buf, tb, c, l, j, par ? K::odd_pos(k) : K::even_pos(k), A, B);
                 const double m2 = e.x * e.x + e.y * e.y;
                 n2 += m2;
                 rr += (double)j * tb.dr * m2;
@@ -689,7 +692,7 @@ template <typename T, int N, int V> struct Pointwise {
                 for (int k = g; k < N / 2; k += G)
                     for (int par = 0; par < 2; ++par) {
                         const int j = 2 * k + par;
-                        const cpx<double> e = end_value(buf, tb, c, l, j, par ? K::odd_pos(k) : k, A, B);
+                        const cpx<double> e = end_value(buf, tb, c, l, j, par ? K::odd_pos(k) : K::even_pos(k), A, B);
                         const double ph = tb.eig[(size_t)s * N + j];
                         vr += ph * e.x;
                         vi += ph * e.y;
@@ -709,7 +712,7 @@ template <typename T, int N, int V> struct Pointwise {
         for (int k = g; k < N / 2; k += G) {
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
-                const int p = par ? K::odd_pos(k) : k;
+                const int p = par ? K::odd_pos(k) : K::even_pos(k);
                 const T fj = (T)j, j2 = fj * fj;
                 T sn, cs;
                 k_sincospi(B * j2, &sn, &cs);
@@ -726,7 +729,7 @@ template <typename T, int N, int V> struct Pointwise {
         for (int k = g; k < N / 2; k += G) {
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
-                const int p = par ? K::odd_pos(k) : k;
+                const int p = par ? K::odd_pos(k) : K::even_pos(k);
                 buf[p] = scale(buf[p], (T)j * s);
             }
         }
@@ -826,13 +829,13 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         if (tb.ic_cplx) {
             const double *ic = tb.ic + (size_t)d.spec * 2 * N;
             for (int k = g; k < N / 2; k += G) {
-                buf[k] = mk<T>((T)ic[4 * k], (T)ic[4 * k + 1]);
+                buf[K::even_pos(k)] = mk<T>((T)ic[4 * k], (T)ic[4 * k + 1]);
                 buf[K::odd_pos(k)] = mk<T>((T)ic[4 * k + 2], (T)ic[4 * k + 3]);
             }
         } else {
             const double *ic = tb.ic + (size_t)d.spec * N;
             for (int k = g; k < N / 2; k += G) {
-                buf[k] = mk<T>((T)ic[2 * k], (T)0);
+                buf[K::even_pos(k)] = mk<T>((T)ic[2 * k], (T)0);
                 buf[K::odd_pos(k)] = mk<T>((T)ic[2 * k + 1], (T)0);
             }
         }
@@ -935,7 +938,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         // observables (FP64)
         double acc = 0.0;
         for (int k = g; k < N / 2; k += G) {
-            const cpx<T> a0 = buf[k], a1 = buf[K::odd_pos(k)];
+            const cpx<T> a0 = buf[K::even_pos(k)], a1 = buf[K::odd_pos(k)];
             acc += (double)a0.x * a0.x + (double)a0.y * a0.y + (double)a1.x * a1.x + (double)a1.y * a1.y;
         }
         const double n2 = slot_sum<G>(acc, red) * dr;
@@ -949,7 +952,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             const double *phi = tb.eig + (size_t)s * N;
             double pr = 0.0, pi = 0.0;
             for (int k = g; k < N / 2; k += G) {
-                const cpx<T> a0 = buf[k], a1 = buf[K::odd_pos(k)];
+                const cpx<T> a0 = buf[K::even_pos(k)], a1 = buf[K::odd_pos(k)];
                 const double f0 = phi[2 * k], f1 = phi[2 * k + 1];
                 pr += f0 * (double)a0.x + f1 * (double)a1.x;
                 pi += f0 * (double)a0.y + f1 * (double)a1.y;
@@ -960,7 +963,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         if (a.states) {
             double *st = a.states + (size_t)t * N * 2;
             for (int k = g; k < N / 2; k += G) {
-                const cpx<T> a0 = buf[k], a1 = buf[K::odd_pos(k)];
+                const cpx<T> a0 = buf[K::even_pos(k)], a1 = buf[K::odd_pos(k)];
                 st[4 * k] = (double)a0.x;
                 st[4 * k + 1] = (double)a0.y;
                 st[4 * k + 2] = (double)a1.x;
