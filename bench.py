@@ -41,7 +41,7 @@ UNIT = "traj-steps/s"
 N_GRID, L_BOX, DT = 4096, 40.0, 0.001
 # DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture of the current
 # kernel source (None until the kernel has been captured again after a change)
-PROFILED_DRAM_BYTES_PER_TRAJ_STEP = None
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 7.71
 N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
