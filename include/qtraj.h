@@ -130,8 +130,10 @@ typedef struct {
 
 /* Create a context for an N-point grid on (0, L] with step dt and heavy-quark mass M (Table 1:
  * num, L, dt, m).  N must be a power of two in [16, 16384] (FP64 fused: <= 8192).  Builds the
- * read-only tables on the current CUDA device; synchronous.  EINVAL on N/L/dt/M/params out of
- * range (alpha_s < 0, Nc < 2, r_max not in (0,1], deriv_type not 0/1, FP32 with the plain form). */
+ * read-only tables on the current CUDA device (the static potential factors of both colours for
+ * l < 256 take 16 KiB x N: 256 MiB at N = 16384); synchronous.  EINVAL on N/L/dt/M/params out of
+ * range (alpha_s < 0, Nc < 2, r_max not in (0,1], deriv_type not 0/1, FP32 with the plain form);
+ * ENOMEM if the tables do not fit in device memory. */
 qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_params *params, qtraj_ctx **out);
 
 /* Frees the context and its tables (synchronises the device first).  NULL is a no-op. */

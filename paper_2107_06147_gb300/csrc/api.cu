@@ -224,8 +224,11 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
     CK(cudaMalloc(&c->KT, sizeof(PC) * N));
     CK(cudaMalloc(&c->sinpre, sizeof(PR) * N));
     const size_t nstat = (size_t)2 * LTAB * N;
-    CK(cudaMalloc(&c->statV, sizeof(PC) * nstat));
-    CK(cudaMalloc(&c->statV2, sizeof(PC) * nstat));
+    if (cudaMalloc(&c->statV, sizeof(PC) * nstat) != cudaSuccess ||
+        cudaMalloc(&c->statV2, sizeof(PC) * nstat) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QTRAJ_ENOMEM, "cudaMalloc of the static space-kernel tables (%zu bytes)", 2 * sizeof(PC) * nstat);
+    }
     CK(cudaMemcpy(c->W, W.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->KT, KT.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->sinpre, sp.data(), sizeof(PR) * N, cudaMemcpyHostToDevice));
