@@ -562,8 +562,8 @@ def test_uneven_batch_against_oracle(q, precision):
         assert np.abs(obs["surv"].mean(0) - ref["surv"].mean(0)).max() <= FP32_ENSEMBLE_ABS
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_high_l_table_edge(q, precision):
+@pytest.mark.parametrize("precision,form", [(0, 0), (1, 0), (0, 1)])
+def test_high_l_table_edge(q, precision, form):
     """Angular momenta at the edge of the static-factor table (rows l < 256 are tabulated, larger l
     evaluated on the fly) and beyond it: singlet and octet Gaussians r^{l+1} e^{-r^2/(2 0.2^2)}
     (peak near r = 3.3) with l = 254 .. 257 and 300 on N = 1024, L = 10, in media strong enough
@@ -577,7 +577,7 @@ def test_high_l_table_edge(q, precision):
     assert (ref["n_jumps"] >= 3).mean() > 0.5
     crossed = [(i, l) for i, l in zip(w.init_idx, ref["l"]) if (w.inits[i].l < 256) != (l < 256)]
     assert len(crossed) >= 3, crossed
-    obs, u = run_gpu(q, w, precision)
+    obs, u = run_gpu(q, w, precision, form=q.PLAIN if form else q.FUSED)
     if precision == 0:
         check_fp64(q, obs, ref, u, uref)
     else:
