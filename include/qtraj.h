@@ -257,8 +257,10 @@ qtraj_status qtraj_fma_peak(int precision, double *tflops);
  *     memory and forgets the request.
  * A trajectory's record depends only on its descriptor, never on its launch mates.  Every launch
  * is the fused form with the rMin shortcut off (launches mix many (state, medium) groups); the
- * other fields of `params` apply.  Errors: QTRAJ_EINVAL for a grid size not served, a catalogue
- * index out of range, an invalid medium (as in qtraj_evolve), n <= 0, or an id already queued or
+ * other fields of `params` apply.  Media are Bjorken (kind 0; a lattice-fit kappa_hat is allowed);
+ * tabulated profiles need a context's profile store and are not served.  Errors: QTRAJ_EINVAL for
+ * a grid size not served, a catalogue index out of range, an invalid medium (as in qtraj_evolve;
+ * kind 1 always, the slots having no profile store), n <= 0, or an id already queued or
  * not yet returned (checked in qtraj_submit, before anything is queued); QTRAJ_ECUDA from qtraj_poll
  * if a launch failed.  One host thread at a time per server.
  * --------------------------------------------------------------------------------------------- */

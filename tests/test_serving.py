@@ -143,6 +143,10 @@ def test_server_errors():
     bad = d.copy()
     bad["kappa_hat"][1] = -0.5
     assert lib.qtraj_submit(srv.h, C.c_void_p(bad.ctypes.data), len(bad), 5) == 1          # invalid medium
+    bad = d.copy()
+    bad["kind"][2], bad["table_offset"][2], bad["table_len"][2] = 1, 0, 4
+    assert lib.qtraj_submit(srv.h, C.c_void_p(bad.ctypes.data), len(bad), 5) == 1          # tabulated medium
+    assert b"profile store" in lib.qtraj_last_error(None)
     assert lib.qtraj_submit(srv.h, C.c_void_p(d.ctypes.data), len(d), 5) == 0
     assert lib.qtraj_submit(srv.h, C.c_void_p(d.ctypes.data), len(d), 5) == 1              # id already queued
     out = np.zeros(len(d), dtype=qtraj.OBS_DTYPE)
