@@ -262,7 +262,8 @@ qtraj_status qtraj_fma_peak(int precision, double *tflops);
  * a grid size not served, a catalogue index out of range, an invalid medium (as in qtraj_evolve;
  * kind 1 always, the slots having no profile store), n <= 0, or an id already queued or
  * not yet returned (checked in qtraj_submit, before anything is queued); QTRAJ_ECUDA from qtraj_poll
- * if a launch failed.  One host thread at a time per server.
+ * if a launch failed, after which the requests of that launch never finish and the server is to be
+ * destroyed.  One host thread at a time per server.
  * --------------------------------------------------------------------------------------------- */
 typedef struct qtraj_server qtraj_server;
 
