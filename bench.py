@@ -449,8 +449,10 @@ def run_profile_case(args):
     import torch
 
     from paper_2107_06147_gb300 import inputs, qtraj
-    w = inputs.uniform_interleaved(per_group=10000, N=N_GRID, L=L_BOX, dt=DT)
-    probe = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=qtraj.FP32 if args.precision == "fp32"
+    NG = args.profile_n
+    LB = NG * L_BOX / N_GRID          # the same dr as the bench workload
+    w = inputs.uniform_interleaved(per_group=10000, N=NG, L=LB, dt=DT)
+    probe = qtraj.Engine(qtraj.Config(N=NG, L=LB, dt=DT, precision=qtraj.FP32 if args.precision == "fp32"
                                       else qtraj.FP64, variant=args.variant))
     ki = probe.kernel_info()
     probe.close()
@@ -460,7 +462,7 @@ def run_profile_case(args):
     media = [qtraj.medium(m.T0, m.tau0, m.T0 * (m.tau0 / tau_end) ** (1 / 3) * (1 + 1e-9), m.kappa_hat, m.gamma_hat)
              for m in w.media]
     prec = qtraj.FP32 if args.precision == "fp32" else qtraj.FP64
-    eng = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, form=qtraj.FUSED, use_rmin=0,
+    eng = qtraj.Engine(qtraj.Config(N=NG, L=LB, dt=DT, precision=prec, form=qtraj.FUSED, use_rmin=0,
                                     variant=args.variant))
     specs = [qtraj.init_spec(s.kind, s.width, s.n, s.l, s.color) for s in w.inits]
     eng.init(specs, B, spec_idx=w.init_idx[:B])
@@ -468,7 +470,7 @@ def run_profile_case(args):
         eng.evolve(media, w.seeds[:B], w.medium_idx[:B])
     torch.cuda.synchronize()
     s = eng.stats()
-    print(json.dumps({"profile_case": True, "trajectories": B, "steps_executed": int(s.steps_executed),
+    print(json.dumps({"profile_case": True, "N": NG, "trajectories": B, "steps_executed": int(s.steps_executed),
                       "ms": round(s.ms_main, 3), "traj_steps_per_s": round(s.steps_executed / (s.ms_main / 1e3), 1)}))
     eng.close()
 
@@ -490,6 +492,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
     ap.add_argument("--profile-steps", type=int, default=1000)
+    ap.add_argument("--profile-n", type=int, default=N_GRID, help="grid size of --profile-case (dr of the bench workload)")
     ap.add_argument("--uneven", type=int, default=0, metavar="NTRAJ",
                     help="throughput of the uneven-batch workload (NTRAJ trajectories of mixed N, l, lifetime)")
     ap.add_argument("--serving-sweep", default="", metavar="RATES",
