@@ -264,6 +264,14 @@ def run_ours(args):
         result["plain_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.PLAIN, args.compare_batch)
         result["fused_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.FUSED, args.compare_batch)
         result["speedup_vs_plain_fp64"] = round(value / world / result["plain_fp64"]["value"], 2)
+        # the FP64 forms are bound by GB300's FP64 pipe: their algorithmic rate against the FP64 FMA
+        # throughput measured on the same GPU
+        fma64 = qtraj.fma_peak(qtraj.FP64)
+        result["fp64_fma_peak_measured_tflops"] = round(fma64, 3)
+        for k in ("plain_fp64", "fused_fp64"):
+            t = result[k]["value"] * alg / 1e12
+            result[k]["tflops"] = round(t, 4)
+            result[k]["frac_of_measured_fp64_fma"] = round(t / fma64, 4)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
     if rank == 0 and world == 1 and not args.no_serving:
