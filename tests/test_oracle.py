@@ -106,6 +106,26 @@ def test_jump_matrix_matches_paper(oracle_lib):
         assert abs(f - p) < 4 * np.sqrt(p * (1 - p) / 50000)
 
 
+def test_jump_rule_at_large_l(oracle_lib):
+    """Eq. (pjump) beyond the printed matrix: for every l up to 300 the oracle jumps down with
+    probability l/(2l+1) (threshold found by bisection on u_l), so that l(l+1) grows by exactly 2 per
+    jump on average, (l+1)/(2l+1) (l+1)(l+2) + l/(2l+1) (l-1)l - l(l+1) = 2 -- the growth that takes
+    trajectories with hundreds of jumps to l ~ 30..130."""
+    o = oracle_lib
+    for l in list(range(0, 40)) + [63, 64, 65, 127, 128, 255, 256, 257, 300]:
+        lo, hi = 0.0, 1.0
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if o.jump_l(l, mid) == l - 1:
+                lo = mid
+            else:
+                hi = mid
+        p_down = lo
+        assert abs(p_down - l / (2 * l + 1)) < 1e-12, l
+        growth = (1 - p_down) * (l + 1) * (l + 2) + p_down * (l - 1) * l - l * (l + 1)
+        assert abs(growth - 2.0) < 1e-6 * max(1, l * l), (l, growth)
+
+
 def test_colour_rule_and_potential_constants(oracle_lib):
     o = oracle_lib
     g = o.Grid()
