@@ -4,13 +4,22 @@ Trajectories are grouped by grid size N (a kernel instantiation and its shared-m
 depend on N); each group runs as one persistent fused launch on its own CUDA stream, and all groups
 are launched before any of them is waited for, so they share the GPU.  Inside a launch the CTAs take
 trajectories from the launch's work counter, so trajectories of different l and different lifetimes
-(media) refill the CTAs as they finish.  Results come back in the caller's order.
+(media) refill the CTAs as they finish; a group is ordered longest medium first (Bjorken media;
+tabulated ones keep their place), so that the last trajectories to start are short ones and the
+launch's tail is short.  Results come back in the caller's order.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from . import qtraj
+
+
+def _lifetime(m) -> float:
+    """Proper-time span of a Bjorken medium, tau0 ((T0/Tf)^3 - 1) (fm/c); 0 for a tabulated one."""
+    if m.kind == 0 and m.Tf > 0 and m.T0 > m.Tf:
+        return m.tau0 * ((m.T0 / m.Tf) ** 3 - 1.0)
+    return 0.0
 
 
 class UnevenBatch:
@@ -24,6 +33,7 @@ class UnevenBatch:
         self.groups = []
         for N in sorted(set(int(x) for x in Ns)):
             ids = np.nonzero(Ns == N)[0]
+            ids = ids[np.argsort([-_lifetime(media[t]) for t in ids], kind="stable")]
             L = float(Ls[ids[0]]) if Ls is not None else N * dr
             spec_keys, spec_list, spec_idx = {}, [], []
             for t in ids:
