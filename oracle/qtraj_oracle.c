@@ -339,14 +339,22 @@ void oqt_initial_state(const oqt_params *p, const oqt_init *in, double complex *
         free(phi);
         return;
     }
-    double s = 0;
-    u[0] = 0;
+    /* the Gaussian through its logarithm, less the largest logarithm (the same normalised state;
+       r^{l+1} alone would overflow at large l) */
+    double *e = malloc(sizeof(double) * p->N);
+    double emax = -HUGE_VAL, s = 0;
     for (int j = 1; j < p->N; j++) {
         double r = j * dr;
-        double v = pow(r, in->l + 1) * exp(-r * r / (2.0 * in->width * in->width));
+        e[j] = (in->l + 1) * log(r) - r * r / (2.0 * in->width * in->width);
+        if (e[j] > emax) emax = e[j];
+    }
+    u[0] = 0;
+    for (int j = 1; j < p->N; j++) {
+        double v = exp(e[j] - emax);
         u[j] = v;
         s += v * v;
     }
+    free(e);
     double c = 1.0 / sqrt(s * dr);
     for (int j = 1; j < p->N; j++) u[j] *= c;
 }

@@ -78,18 +78,12 @@ void coulomb_u(int N, double dr, double a0, int n, int l, std::vector<double> &u
     for (int j = 1; j < N; ++j) u[j] *= c;
 }
 
+void st_gauss(int N, double dr, double w, int l, double *u);
+
 void gauss_u(int N, double dr, double w, int l, std::vector<double> &u)
 {
     u.assign(N, 0.0);
-    double s = 0.0;
-    for (int j = 1; j < N; ++j) {
-        const double r = j * dr;
-        const double v = std::pow(r, l + 1) * std::exp(-r * r / (2.0 * w * w));
-        u[j] = v;
-        s += v * v;
-    }
-    const double c = 1.0 / std::sqrt(s * dr);
-    for (int j = 1; j < N; ++j) u[j] *= c;
+    st_gauss(N, dr, w, l, u.data());
 }
 
 } // namespace
@@ -1096,15 +1090,21 @@ void st_coulomb(int N, double dr, double a0, int n, int l, double *u)
     const double c = 1.0 / std::sqrt(s * dr);
     for (int j = 1; j < N; ++j) u[j] *= c;
 }
+// r^{l+1} exp(-r^2/(2 w^2)), discretely normalised: evaluated through its logarithm shifted by the
+// largest value, so that no power of r overflows at large l (the normalisation removes the shift)
 void st_gauss(int N, double dr, double w, int l, double *u)
 {
-    double s = 0.0;
+    double mx = -HUGE_VAL;
     u[0] = 0.0;
     for (int j = 1; j < N; ++j) {
         const double r = j * dr;
-        const double v = std::pow(r, l + 1) * std::exp(-r * r / (2.0 * w * w));
-        u[j] = v;
-        s += v * v;
+        u[j] = (l + 1) * std::log(r) - r * r / (2.0 * w * w);
+        mx = std::max(mx, u[j]);
+    }
+    double s = 0.0;
+    for (int j = 1; j < N; ++j) {
+        u[j] = std::exp(u[j] - mx);
+        s += u[j] * u[j];
     }
     const double c = 1.0 / std::sqrt(s * dr);
     for (int j = 1; j < N; ++j) u[j] *= c;

@@ -565,13 +565,14 @@ def test_uneven_batch_against_oracle(q, precision):
 @pytest.mark.parametrize("precision,form", [(0, 0), (1, 0), (0, 1)])
 def test_high_l_table_edge(q, precision, form):
     """Angular momenta at the edge of the static-factor table (rows l < 256 are tabulated, larger l
-    evaluated on the fly) and beyond it: singlet and octet Gaussians r^{l+1} e^{-r^2/(2 0.2^2)}
-    (peak near r = 3.3) with l = 254 .. 257 and 300 on N = 1024, L = 10, in media strong enough
-    that jumps carry l back and forth across 255/256."""
+    evaluated on the fly) and beyond it: singlet and octet Gaussians r^{l+1} e^{-r^2/(2 w^2)} with
+    l = 254 .. 257 (w = 0.2, peak near r = 3.2) and l = 300 (w = 0.31, peak near r = 5.4, where
+    r^{l+1} alone overflows) on N = 1024, L = 10, in media strong enough that jumps carry l back
+    and forth across 255/256."""
     from paper_2107_06147_gb300 import inputs
     w = inputs.small_parity(N=1024, n_traj=24, seed=21)
     w.grid.L = 10.0
-    w.inits = [inputs.InitSpec("gauss", 0.2, 1, l, c)
+    w.inits = [inputs.InitSpec("gauss", 0.31 if l == 300 else 0.2, 1, l, c)
                for l, c in ((254, 0), (255, 1), (256, 0), (257, 1), (255, 0), (300, 1))]
     ref, uref = run_oracle(w)
     assert (ref["n_jumps"] >= 3).mean() > 0.5

@@ -126,6 +126,25 @@ def test_jump_rule_at_large_l(oracle_lib):
         assert abs(growth - 2.0) < 1e-6 * max(1, l * l), (l, growth)
 
 
+def test_gaussian_initial_state_at_large_l(oracle_lib):
+    """The Gaussian initial state r^{l+1} e^{-r^2/(2 w^2)}, discretely normalised: at small l equal to
+    the formula evaluated directly (1e-13); at l = 300, w = 0.31, where r^{l+1} alone overflows, finite,
+    normalised, and peaked at the maximum of (l+1) ln r - r^2/(2 w^2), r = w sqrt(l+1) (to one dr)."""
+    o = oracle_lib
+    g = o.Grid(N=1024, L=10.0)
+    dr = g.L / g.N
+    r = np.arange(g.N) * dr
+    for l, w in ((0, 0.2), (2, 0.3), (20, 0.3)):
+        u = o.initial_state(g, o.init_spec("gauss", w, 1, l, 0)).real
+        v = r ** (l + 1) * np.exp(-r * r / (2 * w * w))
+        v /= np.sqrt((v * v).sum() * dr)
+        assert np.abs(u - v).max() < 1e-13 * np.abs(v).max(), l
+    u = o.initial_state(g, o.init_spec("gauss", 0.31, 1, 300, 0)).real
+    assert np.isfinite(u).all() and u[0] == 0.0
+    assert abs((u * u).sum() * dr - 1.0) < 1e-12
+    assert abs(r[np.argmax(u)] - 0.31 * np.sqrt(301)) <= dr
+
+
 def test_colour_rule_and_potential_constants(oracle_lib):
     o = oracle_lib
     g = o.Grid()
