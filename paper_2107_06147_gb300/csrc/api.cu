@@ -63,19 +63,13 @@ double laguerre(int k, int a, double x)
     return p1;
 }
 
+void st_coulomb(int N, double dr, double a0, int n, int l, double *u);
+
 // discretely normalised Coulomb u_nl = r R_nl on r_j = j dr (j = 0..N-1; u_0 = 0)
 void coulomb_u(int N, double dr, double a0, int n, int l, std::vector<double> &u)
 {
     u.assign(N, 0.0);
-    double s = 0.0;
-    for (int j = 1; j < N; ++j) {
-        const double r = j * dr;
-        const double v = std::pow(r, l + 1) * std::exp(-r / (n * a0)) * laguerre(n - l - 1, 2 * l + 1, 2.0 * r / (n * a0));
-        u[j] = v;
-        s += v * v;
-    }
-    const double c = 1.0 / std::sqrt(s * dr);
-    for (int j = 1; j < N; ++j) u[j] *= c;
+    st_coulomb(N, dr, a0, n, l, u.data());
 }
 
 void st_gauss(int N, double dr, double w, int l, double *u);
