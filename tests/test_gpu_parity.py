@@ -600,12 +600,14 @@ def test_precision_study_small(q):
 
 
 def test_nonfinite_input_is_reported(q):
-    """A malformed input (an initial Gaussian so narrow that its grid norm is zero) makes the norm
-    NaN on the GPU; the trajectory is flagged and qtraj_observables returns QTRAJ_ENONFINITE instead
-    of silently returning garbage.  No GPU fault is involved."""
+    """A malformed input (an initial Gaussian so narrow that 2 w^2 underflows to 0, so that the state
+    evaluates to NaN) makes the norm NaN on the GPU; the trajectory is flagged and
+    qtraj_observables returns QTRAJ_ENONFINITE instead of silently returning garbage.  No GPU fault
+    is involved.  (A merely very narrow Gaussian, w = 1e-30, is a valid state: all its weight on the
+    first grid point.)"""
     import torch
     e = q.Engine(q.Config(N=64, L=2.5, dt=0.001))
-    e.init([q.init_spec("gauss", 1e-30, 1, 0, 0), q.init_spec("gauss", 0.3, 1, 0, 0)], 4,
+    e.init([q.init_spec("gauss", 1e-200, 1, 0, 0), q.init_spec("gauss", 0.3, 1, 0, 0)], 4,
            np.array([0, 1, 0, 1], np.int32))
     e.evolve([q.medium(0.4, 0.6, 0.38, 3.0, -1.0)], np.arange(4, dtype=np.uint64))
     with pytest.raises(q.QtrajError) as ei:
