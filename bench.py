@@ -246,7 +246,8 @@ def run_ours(args):
 
     result = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+              "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64"}[args.precision],
+              "data": "synthetic",
               "config": workload_config(B) | {"parallelism": f"replicas x{world} (disjoint trajectory ids)"},
               "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                       # staged per evolve: a 24-byte record per trajectory and per (state, medium)
