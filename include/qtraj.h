@@ -149,7 +149,9 @@ size_t qtraj_workspace_bytes(const qtraj_ctx *ctx, int n_traj);
 /* Binds the caller's device workspace (>= qtraj_workspace_bytes(ctx, n_traj), 256-byte aligned)
  * and sets the initial states: trajectory t starts in specs[spec_idx[t]] (spec_idx NULL: all use
  * specs[0] when n_specs == 1, else spec t when n_specs == n_traj).  Uploads the normalised initial
- * states and their overlaps with the Coulomb basis (host FP64).  Synchronous. */
+ * states and their overlaps with the Coulomb basis (host FP64).  Synchronous.  EINVAL for a spec
+ * out of range or an initial state that is not finite or has no positive discrete norm (e.g. a
+ * Gaussian whose 2 width^2 underflows to 0). */
 qtraj_status qtraj_init(qtraj_ctx *ctx, void *d_workspace, size_t bytes, int n_traj,
                         const qtraj_init_spec *specs, int n_specs, const int *spec_idx);
 
@@ -194,8 +196,12 @@ qtraj_status qtraj_set_profiles(qtraj_ctx *ctx, const double *tau, const double 
 /* Evolves trajectories [0, batch) of the bound workspace through their media: trajectory t sees
  * media[medium_idx[t]] (same NULL rule as qtraj_init) and draws its waiting-time thresholds and
  * jump choices from Philox4x32-10 keyed by seeds[t] (host array of batch entries).  With use_rmin,
- * first evolves one no-jump trajectory per distinct (initial state, medium) pair.  Asynchronous on
- * `stream`; results are read with qtraj_observables. */
+ * also evolves one no-jump trajectory per distinct (initial state, medium) pair (the rMin shortcut,
+ * Sec. 3.5 item 4a): the plain form runs them first; the fused form runs them as the first work
+ * items of its single launch, and a trajectory taken up after its group's no-jump record is
+ * published, with r0 < p_NoJump, copies it (QTRAJ_F_NOJUMP_SHORTCUT, n_steps_exec = 0), while one
+ * taken up before evolves its whole medium -- the same record, since the shortcut is exact, with its
+ * steps counted.  Asynchronous on `stream`; results are read with qtraj_observables. */
 qtraj_status qtraj_evolve(qtraj_ctx *ctx, int batch, const qtraj_medium *media, int n_media, const int *medium_idx,
                           const uint64_t *seeds, void *stream);
 
@@ -213,7 +219,8 @@ qtraj_status qtraj_nojump_results(qtraj_ctx *ctx, qtraj_obs *out_host, int capac
 
 /* Counters of the last evolve: steps executed (sum over trajectories, including the no-jump runs),
  * trajectories run / short-cut, kernel launches, and the device time of the step kernels measured
- * with events on the caller's stream (valid after a synchronising call). */
+ * with events on the caller's stream (valid after a synchronising call): ms_nojump is the plain
+ * form's separate no-jump phase (0 for the fused form, whose no-jump runs share the main launch). */
 typedef struct {
     int64_t steps_executed;
     int64_t nojump_steps;
@@ -235,6 +242,21 @@ qtraj_status qtraj_kernel_info_get(const qtraj_ctx *ctx, qtraj_kernel_info *out)
  * independent FMA chains, 8 blocks of 256 threads per SM, best of 3 timed launches after a warm-up.
  * The achievable denominator of a roofline for ALU-bound kernels.  Synchronous; allocates 8 bytes. */
 qtraj_status qtraj_fma_peak(int precision, double *tflops);
+
+/* The generator of the waiting-time algorithm (Sec. 3.2.1, Eq. wta, and the jump choices of
+ * Sec. 3.4.2 and Eq. Pl+-; the paper's program calls an unnamed Random()): Philox4x32-10 (Salmon,
+ * Moraes, Dror, Shaw, SC'11), computed by the same device code the trajectory kernels run, for
+ * checking it against an independent implementation.
+ *   qtraj_philox4x32_10: for i < n, the four output words of counter d_ctr[4i .. 4i+3] under key
+ *     d_key[2i], d_key[2i+1], into d_out[4i .. 4i+3];
+ *   qtraj_period_draws: for i < n, the three uniforms of waiting period d_k[i] of the trajectory
+ *     with seed d_seed[i] (counter (k, 0, 0, 0), key = the seed's low and high words): the
+ *     threshold r = ((((w1 << 32) | w0) >> 11) + 1/2) 2^-53 and u_l = (w2 + 1/2) 2^-32,
+ *     u_c = (w3 + 1/2) 2^-32, into d_out[3i .. 3i+2].
+ * All buffers are caller device memory.  Asynchronous on `stream`.  EINVAL for n < 0 or a null
+ * buffer with n > 0. */
+qtraj_status qtraj_philox4x32_10(const uint32_t *d_ctr, const uint32_t *d_key, int n, uint32_t *d_out, void *stream);
+qtraj_status qtraj_period_draws(const uint64_t *d_seed, const uint32_t *d_k, int n, double *d_out, void *stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Serving: continuous batching of trajectory requests.  (The paper has no counterpart: its program
@@ -320,8 +342,14 @@ void qtraj_server_destroy(qtraj_server *srv);
  * the device current; make that first call before any stream capture.  All calls share the one array
  * (the work counter and status word are cleared by every call): calls whose GPU work overlaps -- on
  * different streams, or from different host threads without ordering -- race on it and must be
- * serialised by the caller (the host side of the call is serialised by a lock).  Asynchronous on
- * `stream`; the host arrays may be reused when the call returns.
+ * serialised by the caller (the host side of the call is serialised by a lock).  The context's
+ * device must be the current device (QTRAJ_EINVAL otherwise).  The call copies its inputs to the
+ * device array from the library's fixed host arrays, which are pageable memory: each copy first
+ * waits for the work already queued on `stream`, so the call returns once earlier work on `stream`
+ * has finished and its inputs are on their way; the evolve itself is then queued on `stream` and
+ * not waited for.  The caller's host arrays may be reused when the call returns.  An initial state
+ * that is not finite or has no positive norm (e.g. a Gaussian whose 2 width^2 underflows) is
+ * refused with QTRAJ_EINVAL before any GPU work.
  * --------------------------------------------------------------------------------------------- */
 #define QTRAJ_STATIC_MAX_TRAJ 4096
 #define QTRAJ_STATIC_MAX_SPECS 8

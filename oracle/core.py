@@ -80,6 +80,8 @@ def lib():
         L.oqt_dft.argtypes = [C.c_int, cd, cd, C.c_int]
         L.oqt_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.oqt_draws.argtypes = [C.c_uint64, C.c_uint32, cd, cd, cd]
+        L.oqt_philox_many.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.oqt_draws_many.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oqt_bohr_radius.argtypes = [C.POINTER(Params)]
         L.oqt_bohr_radius.restype = C.c_double
         L.oqt_n_steps.argtypes = [C.POINTER(Params), C.POINTER(Medium)]
@@ -205,6 +207,24 @@ def philox4x32_10(ctr, key) -> tuple:
     o = (C.c_uint32 * 4)()
     lib().oqt_philox4x32_10(c, k, o)
     return tuple(o)
+
+
+def philox_many(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    """Philox4x32-10 words of n (counter, key) pairs: ctr (n, 4), key (n, 2) uint32 -> (n, 4) uint32."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros((len(c), 4), dtype=np.uint32)
+    lib().oqt_philox_many(len(c), c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def draws_many(seeds: np.ndarray, k: np.ndarray) -> np.ndarray:
+    """The (r, u_l, u_c) uniforms of waiting period k[i] of seed seeds[i] -> (n, 3) float64."""
+    s = np.ascontiguousarray(seeds, dtype=np.uint64)
+    kk = np.ascontiguousarray(k, dtype=np.uint32)
+    out = np.zeros((len(s), 3))
+    lib().oqt_draws_many(len(s), s.ctypes.data, kk.ctypes.data, out.ctypes.data)
+    return out
 
 
 def draws(seed: int, k: int):

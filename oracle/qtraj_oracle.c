@@ -24,7 +24,7 @@
  *   - survival ratios of the 1S, 2S, 1P, 3S, 2P, 1D Coulomb states (Sec. 5 and the ratios.tsv
  *     format of App. C with its footnote on zero initial overlaps).
  *
- * Readings where the paper is silent or garbled (each one is listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   hbar*c = 0.1973269804 GeV fm converts dt (GeV^-1) to fm/c; n_steps = ceil((tau_f-tau0)/(hbar c dt))
  *   with tau_f = tau0 (T0/Tf)^3; the generator is Philox4x32-10 keyed by the 64-bit trajectory seed with
  *   counter (k,0,0,0) for waiting period k; jumps may trigger after the final step; overlaps are taken
@@ -173,6 +173,19 @@ void oqt_draws(uint64_t seed, uint32_t k, double *r, double *ul, double *uc)
     *r = ((double)(w >> 11) + 0.5) * 0x1.0p-53;
     *ul = ((double)x[2] + 0.5) * 0x1.0p-32;
     *uc = ((double)x[3] + 0.5) * 0x1.0p-32;
+}
+
+/* the same over arrays: the words of n (counter, key) pairs, and the uniforms of n (seed, k) pairs
+ * (for comparing long streams with another implementation without a call per value) */
+void oqt_philox_many(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    for (int i = 0; i < n; i++) oqt_philox4x32_10(ctr + 4 * (size_t)i, key + 2 * (size_t)i, out + 4 * (size_t)i);
+}
+
+void oqt_draws_many(int n, const uint64_t *seed, const uint32_t *k, double *out)
+{
+    for (int i = 0; i < n; i++)
+        oqt_draws(seed[i], k[i], out + 3 * (size_t)i, out + 3 * (size_t)i + 1, out + 3 * (size_t)i + 2);
 }
 
 /* ------------------------------------------------------------------------------------------ */

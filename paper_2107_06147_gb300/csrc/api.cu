@@ -74,6 +74,19 @@ void coulomb_u(int N, double dr, double a0, int n, int l, std::vector<double> &u
 
 void st_gauss(int N, double dr, double w, int l, double *u);
 
+// nullptr if the N values of an initial state are finite with a positive discrete norm, else why
+// not (a Gaussian whose 2 w^2 underflows, for instance, evaluates to NaN)
+const char *state_problem(int N, double dr, const double *u)
+{
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) {
+        if (!std::isfinite(u[j])) return "is not finite";
+        s += u[j] * u[j];
+    }
+    if (!(s * dr > 0.0) || !std::isfinite(s * dr)) return "has no finite positive norm";
+    return nullptr;
+}
+
 void gauss_u(int N, double dr, double w, int l, std::vector<double> &u)
 {
     u.assign(N, 0.0);
@@ -109,7 +122,8 @@ struct qtraj_ctx {
     char *ws = nullptr;
     size_t ws_bytes = 0;
     int n_traj = 0;
-    size_t off_trajs = 0, off_obs = 0, off_gtrajs = 0, off_gobs = 0, off_ctr = 0, off_states = 0, off_plain = 0;
+    size_t off_trajs = 0, off_obs = 0, off_gtrajs = 0, off_gobs = 0, off_gready = 0, off_ctr = 0, off_states = 0,
+           off_plain = 0;
     // host staging and timing
     void *h_stage = nullptr;
     size_t h_stage_bytes = 0;
@@ -123,7 +137,7 @@ struct qtraj_ctx {
 namespace {
 
 struct Layout {
-    size_t trajs, obs, gtrajs, gobs, ctr, states, plain, total;
+    size_t trajs, obs, gtrajs, gobs, gready, ctr, states, plain, total;
 };
 
 Layout layout(const qtraj_ctx *c, int n)
@@ -138,6 +152,8 @@ Layout layout(const qtraj_ctx *c, int n)
     o = align256(o + sizeof(TrajDev) * (size_t)n);
     L.gobs = o;
     o = align256(o + sizeof(qtraj_obs) * (size_t)n);
+    L.gready = o;
+    o = align256(o + sizeof(int) * (size_t)n);
     L.ctr = o;
     o = align256(o + 256);
     L.states = o;
@@ -331,6 +347,9 @@ const char *medium_check(const qtraj_medium &q, const double *prof = nullptr, in
     } else if (!(q.T0 > 0) || !(q.tau0 > 0) || !(q.Tf > 0)) {
         return "T0, tau0, Tf must be positive";
     }
+    if (!std::isfinite(q.kappa_hat) || !std::isfinite(q.gamma_hat) || !std::isfinite(q.Tf) ||
+        (q.kind == 0 && (!std::isfinite(q.T0) || !std::isfinite(q.tau0))))
+        return "the medium's parameters must be finite";
     if (!(q.gamma_hat <= 0)) return "gamma_hat <= 0 required";
     if (kappa_fit_index(q.kappa_hat) != 0) {
         if (!(q.Tf >= 0.155)) return "a kappa_hat lattice fit needs Tf >= T_c = 0.155 GeV";
@@ -610,6 +629,8 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
         } else {
             gauss_u(N, c->dr, q.width, q.l, u);
         }
+        if (const char *why = state_problem(N, c->dr, u.data()))
+            return fail(QTRAJ_EINVAL, "spec %d: the initial state %s", s, why);
         std::memcpy(ic.data() + (size_t)s * N, u.data(), sizeof(double) * N);
         sl[s] = q.l;
         sc[s] = q.color;
@@ -656,6 +677,7 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
     c->off_obs = Lw.obs;
     c->off_gtrajs = Lw.gtrajs;
     c->off_gobs = Lw.gobs;
+    c->off_gready = Lw.gready;
     c->off_ctr = Lw.ctr;
     c->off_states = Lw.states;
     c->off_plain = Lw.plain;
@@ -843,26 +865,19 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
         CK(cudaEventRecord(c->ev1, s));
         CK(plain_run(tb, ma, N, max_steps, pb, s, &c->launches));
     } else {
+        // one launch: the groups' no-jump runs are its first work items, and a trajectory takes the
+        // shortcut once its group's record is published (ms_nojump is then 0)
         FusedInfo fi;
-        if (c->p.precision == QTRAJ_FP32) {
-            const Tables<float> tb = tables<float>(c);
-            if (n_groups > 0) {
-                CK(fused_launch_f32(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
-                ++c->launches;
-                CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
-            }
-            CK(cudaEventRecord(c->ev1, s));
-            CK(fused_launch_f32(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
-        } else {
-            const Tables<double> tb = tables<double>(c);
-            if (n_groups > 0) {
-                CK(fused_launch_f64(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
-                ++c->launches;
-                CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
-            }
-            CK(cudaEventRecord(c->ev1, s));
-            CK(fused_launch_f64(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
-        }
+        LaunchArgs fa = ma;
+        fa.group = nullptr;
+        fa.gtrajs = d_gt;
+        fa.n_groups = n_groups;
+        fa.gobs = d_gobs;
+        fa.gready = n_groups > 0 ? (int *)(c->ws + c->off_gready) : nullptr;
+        if (n_groups > 0) CK(cudaMemsetAsync(fa.gready, 0, sizeof(int) * (size_t)n_groups, s));
+        CK(cudaEventRecord(c->ev1, s));
+        if (c->p.precision == QTRAJ_FP32) CK(fused_launch_f32(N, tables<float>(c), fa, c->sm_count, 0, s, &fi, false, c->p.variant));
+        else CK(fused_launch_f64(N, tables<double>(c), fa, c->sm_count, 0, s, &fi, false, c->p.variant));
         ++c->launches;
     }
     CK(cudaEventRecord(c->ev2, s));
@@ -1040,6 +1055,7 @@ struct StaticScratch {
     int ov0_zero[ST_MAX_SPECS * NBASIS];
     int spec_l[ST_MAX_SPECS];
     int spec_color[ST_MAX_SPECS];
+    int gready[ST_MAX_TRAJ];  // published flags of the groups' no-jump records; cleared by every call
     int counter_status[64];   // [0] work counter, [1] status word; cleared by every call
 };
 
@@ -1103,19 +1119,6 @@ void st_gauss(int N, double dr, double w, int l, double *u)
     const double c = 1.0 / std::sqrt(s * dr);
     for (int j = 1; j < N; ++j) u[j] *= c;
 }
-// overlap of a discretely normalised Coulomb state with u, without storing the basis state
-double st_overlap(int N, double dr, double a0, int n, int l, const double *u)
-{
-    double s = 0.0, o = 0.0;
-    for (int j = 1; j < N; ++j) {
-        const double r = j * dr;
-        const double v = std::pow(r, l + 1) * std::exp(-r / (n * a0)) * laguerre(n - l - 1, 2 * l + 1, 2.0 * r / (n * a0));
-        s += v * v;
-        o += v * u[j];
-    }
-    return o / std::sqrt(s * dr) * dr;
-}
-
 } // namespace
 
 extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj_init_spec *specs, int n_specs,
@@ -1143,6 +1146,9 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
     std::lock_guard<std::mutex> lock(g_static_mutex);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(QTRAJ_ECUDA, "cudaGetDevice failed");
+    // the context's tables live on c->device; the scratch address is looked up on the current one
+    if (dev != c->device)
+        return fail(QTRAJ_EINVAL, "the current device %d is not the context's device %d", dev, c->device);
     StaticScratch *ds = nullptr;
     const qtraj_status sst = st_setup(dev, &ds);
     if (sst != QTRAJ_OK) return sst;
@@ -1158,12 +1164,23 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
         double *u = h.ic + (size_t)s * N;
         if (q.kind == 1) st_coulomb(N, c->dr, c->a0, q.n, q.l, u);
         else st_gauss(N, c->dr, q.width, q.l, u);
+        if (const char *why = state_problem(N, c->dr, u))
+            return fail(QTRAJ_EINVAL, "spec %d: the initial state %s", s, why);
         h.spec_l[s] = q.l;
         h.spec_color[s] = q.color;
+        // the overlaps and their structural zeros follow the context's basis, as in qtraj_init: an
+        // analytic Coulomb state is orthogonal to the other n only in the analytic basis
+        const bool same_family = q.kind == 1 && c->p.basis == 0;
         for (int b = 0; b < NBASIS; ++b) {
-            const int z = q.color != 0 || q.l != BASIS_L[b] || (q.kind == 1 && q.n != BASIS_N[b]);
+            const int z = q.color != 0 || q.l != BASIS_L[b] || (same_family && q.n != BASIS_N[b]);
             h.ov0_zero[s * NBASIS + b] = z;
-            h.ov0[(s * NBASIS + b) * 2] = z ? 0.0 : st_overlap(N, c->dr, c->a0, BASIS_N[b], BASIS_L[b], u);
+            double o = 0.0;
+            if (!z) {
+                const double *ph = c->basis_host.data() + (size_t)b * N;
+                for (int j = 1; j < N; ++j) o += ph[j] * u[j];
+                o *= c->dr;
+            }
+            h.ov0[(s * NBASIS + b) * 2] = o;
             h.ov0[(s * NBASIS + b) * 2 + 1] = 0.0;
         }
     }
@@ -1206,9 +1223,14 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
     // the work counter and the status word must start at zero in every call
     CK(cudaMemsetAsync(ds->counter_status, 0, sizeof(ds->counter_status), s));
 
+    if (n_groups > 0) CK(cudaMemsetAsync(ds->gready, 0, sizeof(int) * (size_t)n_groups, s));
+
     int *d_ctr = ds->counter_status, *d_status = ds->counter_status + 1;
-    LaunchArgs ga{ds->gtrajs, n_groups, ds->gobs, nullptr, d_ctr, d_status, nullptr, 1};
-    LaunchArgs ma{ds->trajs, batch, d_out, ds->gobs, d_ctr, d_status, nullptr, 0};
+    LaunchArgs ma{ds->trajs, batch, d_out, nullptr, d_ctr, d_status, nullptr, 0};
+    ma.gtrajs = ds->gtrajs;
+    ma.n_groups = n_groups;
+    ma.gobs = ds->gobs;
+    ma.gready = ds->gready;
     FusedInfo fi;
     auto point = [&](auto tb) {
         tb.ic = ds->ic;
@@ -1220,20 +1242,7 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
         tb.media = ds->media;
         return tb;
     };
-    if (c->p.precision == QTRAJ_FP32) {
-        const Tables<float> tb = point(tables<float>(c));
-        if (n_groups > 0) {
-            CK(fused_launch_f32(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
-            CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
-        }
-        CK(fused_launch_f32(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
-    } else {
-        const Tables<double> tb = point(tables<double>(c));
-        if (n_groups > 0) {
-            CK(fused_launch_f64(N, tb, ga, c->sm_count, 0, s, &fi, false, c->p.variant));
-            CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), s));
-        }
-        CK(fused_launch_f64(N, tb, ma, c->sm_count, 0, s, &fi, false, c->p.variant));
-    }
+    if (c->p.precision == QTRAJ_FP32) CK(fused_launch_f32(N, point(tables<float>(c)), ma, c->sm_count, 0, s, &fi, false, c->p.variant));
+    else CK(fused_launch_f64(N, point(tables<double>(c)), ma, c->sm_count, 0, s, &fi, false, c->p.variant));
     return QTRAJ_OK;
 }

@@ -31,6 +31,7 @@
 // so the pre- and post-processing, which pair j with N - j, stay inside a thread's registers.
 // Shared-memory addresses of the FFT passes are padded by one element every R.
 #pragma once
+#include "fused_launch.cuh"
 #include "qtraj_device.cuh"
 
 namespace qt {
@@ -742,28 +743,63 @@ template <typename T, int N, int V> struct Pointwise {
     }
 };
 
-// One thread per CTA takes trajectories from the counter; r0 < p_NoJump and r0 > r_max are resolved
-// here without evolving.
+// the ready flag of a group's no-jump record, with acquire semantics: the record written before the
+// flag was released is visible after it
+__device__ __forceinline__ int group_ready(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// a record written by another CTA of this launch, read past L1
+__device__ __forceinline__ qtraj_obs load_obs_cg(const qtraj_obs *p)
+{
+    static_assert(sizeof(qtraj_obs) % 8 == 0, "qtraj_obs is a whole number of 8-byte words");
+    qtraj_obs o;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&o);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(qtraj_obs) / 8); ++i) dst[i] = __ldcg(src + i);
+    return o;
+}
+
+// One thread per CTA takes work items from the counter: a group's no-jump run (item < n_groups) or a
+// trajectory; r0 < p_NoJump (once the group's record is ready, or from a previous launch's records)
+// and r0 > r_max are resolved here without evolving.
 template <typename T>
 __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
 {
     for (;;) {
-        const int t = atomicAdd(a.counter, 1);
-        if (t >= a.n_traj) return -1;
-        if (a.nojump) return t;
+        const int w = atomicAdd(a.counter, 1);
+        if (w >= a.n_groups + a.n_traj) return -1;
+        if (a.nojump || w < a.n_groups) return w;
+        const int t = w - a.n_groups;
         const TrajDev d = a.trajs[t];
         const Draws dr0 = draws(d.seed, 0u);
         int flags = 0;
         if (tb.use_rmin) {
-            const qtraj_obs &gj = a.group[d.group];
-            if (fabs(dr0.r - gj.norm2) < BORDER_EPS) flags |= QTRAJ_F_BORDERLINE;
-            if (dr0.r < gj.norm2) {
-                qtraj_obs o = gj;
-                o.r0 = dr0.r;
-                o.n_steps_exec = 0;
-                o.flags = flags | QTRAJ_F_NOJUMP_SHORTCUT;
-                a.obs[t] = o;
-                continue;
+            bool have = false;
+            qtraj_obs gj;
+            if (a.gready) {
+                if (group_ready(a.gready + d.group)) {
+                    gj = load_obs_cg(a.gobs + d.group);
+                    have = true;
+                }
+            } else if (a.group) {
+                gj = a.group[d.group];
+                have = true;
+            }
+            if (have) {
+                if (fabs(dr0.r - gj.norm2) < border_eps<T>()) flags |= QTRAJ_F_BORDERLINE;
+                if (dr0.r < gj.norm2) {
+                    qtraj_obs o = gj;
+                    o.r0 = dr0.r;
+                    o.n_steps_exec = 0;
+                    o.flags = flags | QTRAJ_F_NOJUMP_SHORTCUT;
+                    a.obs[t] = o;
+                    continue;
+                }
             }
         }
         if (dr0.r > tb.r_max) {
@@ -780,7 +816,7 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
             a.obs[t] = o;
             continue;
         }
-        return t;
+        return w;
     }
 }
 
@@ -825,11 +861,14 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
     for (;;) {
         if (g == 0) s_traj = fetch_trajectory(tb, a);
         __syncthreads();
-        const int t = s_traj;
+        const int wk = s_traj;
         __syncthreads();
-        if (t < 0) break;
+        if (wk < 0) break;
+        const bool grp = wk < a.n_groups;     // a group's no-jump run of this launch
+        const int t = grp ? wk : wk - a.n_groups;
+        const bool nojump = a.nojump || grp;
 
-        const TrajDev d = a.trajs[t];
+        const TrajDev d = grp ? a.gtrajs[t] : a.trajs[t];
         const MediumDev md = tb.media[d.medium];
         int l = tb.spec_l[d.spec], c = tb.spec_color[d.spec];
         if (tb.ic_cplx) {
@@ -847,10 +886,10 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         }
         uint32_t kdraw = 0;
         Draws dw = draws(d.seed, 0u);
-        const double r0 = a.nojump ? 0.0 : dw.r;
-        double thr = a.nojump ? -1.0 : dw.r;
+        const double r0 = nojump ? 0.0 : dw.r;
+        double thr = nojump ? -1.0 : dw.r;
         int nj = 0, flags = 0, fj = -1, ended = 0, executed = 0;
-        const bool traced = V == 4 && a.trace_every > 0 && t < a.trace_n;
+        const bool traced = V == 4 && !grp && a.trace_every > 0 && t < a.trace_n;
         int nrec = 0;
         const int ns = d.n_steps;
         // per-step scalars in the working precision: T^3 = A / (tau0 + n dtau)
@@ -897,8 +936,8 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                 if (g == 0) atomicOr(a.status, 1);
                 break;
             }
-            if (!a.nojump) {
-                if (fabs(n2 - thr) < BORDER_EPS) flags |= QTRAJ_F_BORDERLINE;
+            if (!nojump) {
+                if (fabs(n2 - thr) < border_eps<T>()) flags |= QTRAJ_F_BORDERLINE;
                 if (n2 <= thr) {
                     // a trajectory stopped by a cap keeps its end-of-step state
                     const bool cap_j = tb.max_jumps >= 0 && nj >= tb.max_jumps;
@@ -966,7 +1005,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             ovr[s] = slot_sum<G>(pr, red) * dr;
             ovi[s] = slot_sum<G>(pi, red) * dr;
         }
-        if (a.states) {
+        if (a.states && !grp) {
             double *st = a.states + (size_t)t * N * 2;
             for (int k = g; k < N / 2; k += G) {
                 const cpx<T> a0 = buf[K::even_pos(k)], a1 = buf[K::odd_pos(k)];
@@ -1001,7 +1040,13 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             o.n_steps_exec = executed;
             o.flags = flags;
             o.first_jump_step = fj;
-            a.obs[t] = o;
+            if (grp) {
+                a.gobs[t] = o;
+                __threadfence();              // the record before the flag that publishes it
+                atomicExch(a.gready + t, 1);
+            } else {
+                a.obs[t] = o;
+            }
             if (traced) a.trace_cnt[t] = nrec;
         }
         __syncthreads();
@@ -1016,6 +1061,41 @@ template <typename T, int N, int V> constexpr int fused_smem_bytes()
            (tw_entries(P::R * P::M1) + P::TW2) *
                (int)sizeof(typename Prec<T>::C) +
            (P::G / 32 + 1) * (int)sizeof(Carry<T>) + (P::G / 32 + 1) * 8 + 16;
+}
+
+// Launches fused_kernel<T, N, V> as one persistent wave (SMs x resident CTAs, at most max_ctas when
+// max_ctas > 0, at most one CTA per trajectory) after setting its shared-memory size; fills info
+// (query_only: launches nothing).  Every instantiation unit dispatches its grid sizes to this helper.
+template <typename T, int N, int V>
+cudaError_t fused_go(const Tables<T> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s,
+                     FusedInfo *info, bool query_only)
+{
+    auto k = fused_kernel<T, N, V>;
+    constexpr int G = FusedPlan<N, V>::G;
+    constexpr int smem = fused_smem_bytes<T, N, V>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, G, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    if (info) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return e;
+        info->G = G;
+        info->R = FusedPlan<N, V>::R;
+        info->smem = smem;
+        info->ctas_per_sm = occ;
+        info->regs = fa.numRegs;
+    }
+    const long work = (long)a.n_traj + a.n_groups;
+    if (query_only || work <= 0) return cudaSuccess;
+    long grid = (long)sm_count * occ;
+    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+    if (grid > work) grid = work;
+    k<<<(int)grid, G, smem, s>>>(tb, a);
+    return cudaGetLastError();
 }
 
 } // namespace qt

@@ -5,58 +5,26 @@
 namespace qt {
 cudaError_t fused_launch_f32_b(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
                              cudaStream_t s, FusedInfo *info, bool query_only, int variant);
-namespace {
-template <int N, int V>
-cudaError_t go(const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas, cudaStream_t s, FusedInfo *info,
-               bool query_only)
-{
-    auto k = fused_kernel<float, N, V>;
-    constexpr int G = FusedPlan<N, V>::G;
-    constexpr int smem = fused_smem_bytes<float, N, V>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, G, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    if (info) {
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, k);
-        if (e != cudaSuccess) return e;
-        info->G = G;
-        info->R = FusedPlan<N, V>::R;
-        info->smem = smem;
-        info->ctas_per_sm = occ;
-        info->regs = fa.numRegs;
-    }
-    if (query_only || a.n_traj <= 0) return cudaSuccess;
-    long grid = (long)sm_count * occ;
-    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
-    if (grid > a.n_traj) grid = a.n_traj;
-    k<<<(int)grid, G, smem, s>>>(tb, a);
-    return cudaGetLastError();
-}
-} // namespace
 
 cudaError_t fused_launch_f32(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
                              cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
     if (a.trace_every > 0) variant = 0;   // the per-step summary runs the traced twin of variant 0
     switch (N) {
-    case 16: return a.trace_every > 0 ? go<16, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
-                                  : go<16, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 32: return a.trace_every > 0 ? go<32, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
-                                  : go<32, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 64: return a.trace_every > 0 ? go<64, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
-                                  : go<64, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 128: return a.trace_every > 0 ? go<128, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
-                                  : go<128, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 256: return a.trace_every > 0 ? go<256, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
-                                  : go<256, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 512: return a.trace_every > 0 ? go<512, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
-                                  : go<512, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 1024: return a.trace_every > 0 ? go<1024, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
-                                  : go<1024, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 16: return a.trace_every > 0 ? fused_go<float, 16, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : fused_go<float, 16, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 32: return a.trace_every > 0 ? fused_go<float, 32, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : fused_go<float, 32, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 64: return a.trace_every > 0 ? fused_go<float, 64, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : fused_go<float, 64, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 128: return a.trace_every > 0 ? fused_go<float, 128, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : fused_go<float, 128, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 256: return a.trace_every > 0 ? fused_go<float, 256, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : fused_go<float, 256, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 512: return a.trace_every > 0 ? fused_go<float, 512, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : fused_go<float, 512, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
+    case 1024: return a.trace_every > 0 ? fused_go<float, 1024, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : fused_go<float, 1024, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
     default: return fused_launch_f32_b(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);
     }
 }

@@ -10,7 +10,16 @@ namespace qt {
 
 constexpr int NBASIS = QTRAJ_NBASIS;
 constexpr int LTAB = 256;            // l rows per colour of the static space-kernel tables
-constexpr double BORDER_EPS = 1e-12; // |norm^2 - r| below this flags a borderline comparison
+constexpr double BORDER_EPS = 1e-12; // |norm^2 - r| below this flags a borderline comparison (FP64)
+// The FP32 forms flag at the error of their norm instead: the state is carried in FP32, and its
+// norm after thousands of steps is good to ~1e-6 (the paired FP32/FP64 study: 3e-4 of the jumps
+// moved by a step, at ~3e-3 mean norm change per step between jumps), so a threshold closer to the
+// norm than that may be crossed a step earlier or later than in exact arithmetic.
+constexpr double BORDER_EPS_F32 = 1e-6;
+template <typename T> __host__ __device__ constexpr double border_eps()
+{
+    return sizeof(T) == 4 ? BORDER_EPS_F32 : BORDER_EPS;
+}
 
 // ------------------------------------------------------------------------------------------------
 // complex numbers
@@ -361,6 +370,14 @@ struct LaunchArgs {
     qtraj_trace_rec *trace; // per-step summary rows [trace_n][trace_cap] (traced kernel; off if trace_every 0)
     int *trace_cnt;         // rows written per traced trajectory
     int trace_every, trace_n, trace_cap;
+    // fused form, one launch for the rMin shortcut: work items [0, n_groups) are the no-jump runs of
+    // the groups (gtrajs -> gobs, then gready[g] = 1), items n_groups + t the trajectories.  A
+    // trajectory fetched after its group's flag is set takes the shortcut; one fetched before runs
+    // its whole medium, which gives the same record (the shortcut is exact) but counts its steps.
+    const TrajDev *gtrajs;
+    int n_groups;
+    qtraj_obs *gobs;
+    int *gready;
 };
 
 // static part of the half-step space kernel for (colour, l, j); rows beyond the table are

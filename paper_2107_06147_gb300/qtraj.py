@@ -109,6 +109,8 @@ _PROTOS = {
     "qtraj_request_result": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int]),
     "qtraj_server_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "qtraj_server_destroy": (None, [C.c_void_p]),
+    "qtraj_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "qtraj_period_draws": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_evolve_static": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(InitSpec), C.c_int, C.POINTER(C.c_int),
                                       C.POINTER(Medium), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint64),
                                       C.c_void_p, C.c_void_p]),
@@ -325,3 +327,26 @@ class Engine:
         k = KernelInfo()
         _check(self.lib.qtraj_kernel_info_get(self.ctx, C.byref(k)), self.ctx)
         return k
+
+
+def philox4x32_10(ctr, key, stream=None):
+    """Philox4x32-10 words of the device generator: ctr (n, 4) and key (n, 2) uint32 torch device
+    tensors in, an (n, 4) uint32 device tensor out (int32 storage)."""
+    import torch
+    n = int(ctr.shape[0])
+    out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    _check(load().qtraj_philox4x32_10(C.c_void_p(ctr.data_ptr()), C.c_void_p(key.data_ptr()), n,
+                                      C.c_void_p(out.data_ptr()), C.c_void_p(_stream_ptr(stream))))
+    return out
+
+
+def period_draws(seeds, k, stream=None):
+    """The (r, u_l, u_c) uniforms of waiting period k[i] of seed seeds[i] (int64 / int32 torch device
+    tensors holding uint64 / uint32 values), as the trajectory kernels draw them: an (n, 3) float64
+    device tensor."""
+    import torch
+    n = int(seeds.shape[0])
+    out = torch.empty((n, 3), dtype=torch.float64, device=seeds.device)
+    _check(load().qtraj_period_draws(C.c_void_p(seeds.data_ptr()), C.c_void_p(k.data_ptr()), n,
+                                     C.c_void_p(out.data_ptr()), C.c_void_p(_stream_ptr(stream))))
+    return out

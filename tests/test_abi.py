@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "qtraj.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(qtraj_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(qtraj_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -45,6 +45,9 @@ def test_library_loads_and_prototypes_cover_the_header(libpath):
     p = qtraj.Config(precision=qtraj.FP32, form=qtraj.PLAIN).params()
     assert lib.qtraj_create(512, 20.0, 0.001, 4.65, ctypes.byref(p), ctypes.byref(h)) == 1
     assert lib.qtraj_workspace_bytes(None, 10) == 0
+    assert lib.qtraj_philox4x32_10(None, None, -1, None, None) == 1
+    assert lib.qtraj_period_draws(None, None, 5, None, None) == 1
+    assert b"null buffer" in lib.qtraj_last_error(None)
 
 
 def test_record_layouts_agree():

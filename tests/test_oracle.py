@@ -312,6 +312,25 @@ def test_nonhermitian_decay_rate(oracle_lib):
         assert 3.0 < errs[0] / errs[1] < 5.0            # second order in dt
 
 
+def test_kappa_fit_coefficients_match_the_printed_fits(oracle_lib):
+    """App. E prints the three lattice fits of kappa_hat(T) coefficient by coefficient
+    (tests/golden/kappa_hat_lattice_fits.txt, transcribed from the paper).  Evaluated at x = T/T_c
+    from 1 to 60 with those printed numbers, the oracle's fit must agree to rounding: a typo in any
+    of the twelve coefficients, a swapped row (the kappa = -1/-2/-3 labels) or another T_c breaks it."""
+    rows = _read_golden("kappa_hat_lattice_fits.txt")
+    assert [r[1] for r in rows] == ["central", "lower", "upper"]
+    x = np.array([1.0, 1.3, 2.0, 3.7, 6.0, 11.0, 25.0, 60.0])
+    for r in rows:
+        which = int(r[0])
+        a, b, c, d = (float(t) for t in r[2:6])
+        printed = 1.0 / (a * x ** 1.5 + b * x + c * np.sqrt(x) + d)
+        got = np.array([oracle_lib.kappa_fit(which, 0.155 * xi) for xi in x])
+        np.testing.assert_allclose(got, printed, rtol=1e-13, atol=0)
+    # and each printed fit is distinct at every x, so the comparison above separates the rows
+    f = np.array([[oracle_lib.kappa_fit(w, 0.155 * xi) for xi in x] for w in (1, 2, 3)])
+    assert (np.abs(np.diff(f, axis=0)) > 1e-3 * np.abs(f[1:])).all()
+
+
 def test_kappa_fits_positive_ordered_decreasing(oracle_lib):
     """The three lattice fits of kappa_hat(T) (App. E; parameter kappa = -1, -2, -3): positive and
     decreasing in T over T_c..100 T_c, and the lower-limit fit below the central below the upper-limit
