@@ -889,6 +889,12 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         const double r0 = nojump ? 0.0 : dw.r;
         double thr = nojump ? -1.0 : dw.r;
         int nj = 0, flags = 0, fj = -1, ended = 0, executed = 0;
+        // r0 > r_max reaches here only when its group's no-jump record was not yet published: the paper
+        // resolves r0 < p_NoJump by the shortcut first and r0 > r_max only otherwise.  The trajectory
+        // is evolved: if its norm never falls to r0 it is the no-jump run (= the shortcut's record); the
+        // first trigger shows r0 >= p_NoJump (the norm only decreases), and it ends as r_max does.
+        const bool rmax_pending = !nojump && dw.r > tb.r_max;
+        bool rmax_hit = false;
         const bool traced = V == 4 && !grp && a.trace_every > 0 && t < a.trace_n;
         int nrec = 0;
         const int ns = d.n_steps;
@@ -938,6 +944,11 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             }
             if (!nojump) {
                 if (fabs(n2 - thr) < border_eps<T>()) flags |= QTRAJ_F_BORDERLINE;
+                if (n2 <= thr && rmax_pending) {
+                    rmax_hit = true;
+                    ended = 1;
+                    break;
+                }
                 if (n2 <= thr) {
                     // a trajectory stopped by a cap keeps its end-of-step state
                     const bool cap_j = tb.max_jumps >= 0 && nj >= tb.max_jumps;
@@ -1040,6 +1051,13 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             o.n_steps_exec = executed;
             o.flags = flags;
             o.first_jump_step = fj;
+            if (rmax_hit) {   // the r_max record, with the steps that found r0 >= p_NoJump
+                for (int s = 0; s < NBASIS; ++s) { o.surv[s] = 0; o.ov_re[s] = 0; o.ov_im[s] = 0; }
+                o.norm2 = 1.0;
+                o.l = tb.spec_l[d.spec];
+                o.color = tb.spec_color[d.spec];
+                o.flags = flags | QTRAJ_F_RMAX;
+            }
             if (grp) {
                 a.gobs[t] = o;
                 __threadfence();              // the record before the flag that publishes it

@@ -61,11 +61,15 @@ def run_oracle(w, **cfg):
 
 
 def lazy_shortcut(q, obs, ref):
-    """Trajectories the oracle resolved with the rMin shortcut (r0 < p_NoJump) that the fused launch
-    evolved through their whole medium because they were taken up before their group's no-jump run
-    had published its record.  The shortcut is exact, so their record is the same; only the executed
-    step count (the medium's, not 0) and the shortcut flag differ."""
-    return ((ref["flags"] & q.F_NOJUMP_SHORTCUT) != 0) & ((obs["flags"] & q.F_NOJUMP_SHORTCUT) == 0)
+    """Trajectories the oracle resolved without evolving -- by the rMin shortcut (r0 < p_NoJump) or
+    by r_max -- that the fused launch evolved because they were taken up before their group's no-jump
+    run had published p_NoJump.  The shortcut is exact, so their record is the same (and an r_max
+    trajectory ends at its first trigger with the r_max record); only the executed step count and the
+    shortcut flag differ."""
+    resolved = (ref["n_steps_exec"] == 0) & ((ref["flags"] & (q.F_NOJUMP_SHORTCUT | q.F_RMAX)) != 0)
+    ours_resolved = ((obs["flags"] & q.F_NOJUMP_SHORTCUT) != 0) | \
+        (((obs["flags"] & q.F_RMAX) != 0) & (obs["n_steps_exec"] == 0))
+    return resolved & ~ours_resolved
 
 
 def same_bookkeeping(q, obs, ref, ok):
@@ -75,7 +79,7 @@ def same_bookkeeping(q, obs, ref, ok):
     for f in ("n_jumps", "first_jump_step", "l", "color"):
         assert np.array_equal(obs[f][ok], ref[f][ok]), (f, obs[f][ok], ref[f][ok])
     assert np.array_equal(obs["n_steps_exec"][ok & ~lazy], ref["n_steps_exec"][ok & ~lazy])
-    assert (obs["n_steps_exec"][ok & lazy] > 0).all() and (obs["n_jumps"][ok & lazy] == 0).all()
+    assert (obs["n_jumps"][ok & lazy] == 0).all() and (obs["first_jump_step"][ok & lazy] == -1).all()
     fr = ref["flags"] & ~q.F_BORDERLINE
     fr[lazy] &= ~q.F_NOJUMP_SHORTCUT
     assert np.array_equal(obs["flags"][ok] & ~q.F_BORDERLINE, fr[ok])
