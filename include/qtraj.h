@@ -119,13 +119,19 @@ typedef struct {
 
 /* Result of one trajectory (the ratios.tsv row of App. C plus bookkeeping).  surv[s] is
  * |<s|psi>|^2 / ||psi||^2 divided by |<s|psi_0>|^2, or undivided when the initial overlap is zero
- * (App. C footnote), and 0 unless the final state is a singlet of the basis state's l. */
+ * (App. C footnote), and 0 unless the final state is a singlet of the basis state's l.
+ * jump_digest identifies the whole jump sequence: 32-bit FNV-1a (offset basis 2166136261, prime
+ * 16777619) over the bytes, little-endian, of the words (step n, new l, new colour) of every jump in
+ * order -- 2166136261 for a trajectory without jumps.  Two runs agree on it exactly when every jump
+ * happened at the same step with the same outcome.  192 bytes. */
 typedef struct {
     double surv[QTRAJ_NBASIS];
     double ov_re[QTRAJ_NBASIS], ov_im[QTRAJ_NBASIS]; /* <s|psi> of the unnormalised final state */
     double norm2;                                    /* final (L/N) sum |u_j|^2                  */
     double r0;                                       /* the first waiting-time threshold         */
     int l, color, n_jumps, n_steps_exec, flags, first_jump_step;
+    int last_jump_step;                              /* step of the last jump, -1 if none        */
+    uint32_t jump_digest;                            /* FNV-1a of the jump sequence (above)      */
 } qtraj_obs;
 
 /* Create a context for an N-point grid on (0, L] with step dt and heavy-quark mass M (Table 1:

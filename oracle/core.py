@@ -55,7 +55,8 @@ class Obs(C.Structure):
     _fields_ = [("surv", C.c_double * NBASIS), ("ov_re", C.c_double * NBASIS),
                 ("ov_im", C.c_double * NBASIS), ("norm2", C.c_double), ("r0", C.c_double),
                 ("l", C.c_int), ("color", C.c_int), ("n_jumps", C.c_int), ("n_steps_exec", C.c_int),
-                ("flags", C.c_int), ("first_jump_step", C.c_int)]
+                ("flags", C.c_int), ("first_jump_step", C.c_int), ("last_jump_step", C.c_int),
+                ("jump_digest", C.c_uint32)]
 
 
 TRACE_DTYPE = np.dtype([("step", "<i4"), ("color", "<i4"), ("l", "<i4"), ("flags", "<i4"), ("norm2", "<f8"),
@@ -64,7 +65,7 @@ TRACE_DTYPE = np.dtype([("step", "<i4"), ("color", "<i4"), ("l", "<i4"), ("flags
 OBS_DTYPE = np.dtype([("surv", "<f8", NBASIS), ("ov_re", "<f8", NBASIS), ("ov_im", "<f8", NBASIS),
                       ("norm2", "<f8"), ("r0", "<f8"), ("l", "<i4"), ("color", "<i4"),
                       ("n_jumps", "<i4"), ("n_steps_exec", "<i4"), ("flags", "<i4"),
-                      ("first_jump_step", "<i4")])
+                      ("first_jump_step", "<i4"), ("last_jump_step", "<i4"), ("jump_digest", "<u4")])
 assert OBS_DTYPE.itemsize == C.sizeof(Obs)
 
 _lib = None

@@ -82,7 +82,31 @@ typedef struct {
     double ov_re[OQT_NBASIS], ov_im[OQT_NBASIS];
     double norm2, r0;
     int l, color, n_jumps, n_steps_exec, flags, first_jump_step;
+    int last_jump_step;      /* -1 if none */
+    uint32_t jump_digest;    /* FNV-1a (32 bit) of the jump sequence, see oqt_digest_jump */
 } oqt_obs;
+
+/* FNV-1a, 32 bit (Fowler, Noll, Vo): h = (h XOR byte) * 16777619 per byte from the offset basis
+ * 2166136261.  A trajectory's jump digest runs over the little-endian bytes of the three words
+ * (step, new l, new colour) of each of its jumps in order; two runs share it when their jump
+ * sequences are identical step for step. */
+#define OQT_FNV_BASIS 2166136261u
+static uint32_t oqt_fnv_bytes(uint32_t h, uint32_t word)
+{
+    unsigned char b[4] = {(unsigned char)(word & 255u), (unsigned char)((word >> 8) & 255u),
+                          (unsigned char)((word >> 16) & 255u), (unsigned char)(word >> 24)};
+    for (int i = 0; i < 4; i++) {
+        h ^= b[i];
+        h *= 16777619u;
+    }
+    return h;
+}
+static uint32_t oqt_digest_jump(uint32_t h, int step, int l, int color)
+{
+    h = oqt_fnv_bytes(h, (uint32_t)step);
+    h = oqt_fnv_bytes(h, (uint32_t)l);
+    return oqt_fnv_bytes(h, (uint32_t)color);
+}
 
 /* one row of the per-step summary (App. C, summary.tsv): after step `step` (1-based), before a jump
  * at that step -- the norm, colour, l, the overlaps |<nl|psi>|^2 of the normalised state (zero unless
@@ -564,6 +588,7 @@ void oqt_nojump_run(const oqt_params *p, const oqt_init *in, const oqt_medium *m
     oqt_finalize(p, &b, u, in->color, in->l, o);
     o->l = in->l; o->color = in->color; o->n_jumps = 0; o->n_steps_exec = ns;
     o->first_jump_step = -1; o->r0 = 0;
+    o->last_jump_step = -1; o->jump_digest = OQT_FNV_BASIS;
     if (!isfinite(o->norm2)) o->flags |= OQT_F_NONFINITE;
     if (u_final) memcpy(u_final, u, sizeof(double complex) * N);
     free(u);
@@ -618,6 +643,8 @@ void oqt_trajectory_traced(const oqt_params *p, const oqt_init *in, const oqt_me
     double dr = p->L / N;
     memset(o, 0, sizeof(*o));
     o->first_jump_step = -1;
+    o->last_jump_step = -1;
+    o->jump_digest = OQT_FNV_BASIS;
     uint32_t k = 0;
     double r, ul, uc;
     oqt_draws(seed, k, &r, &ul, &uc);
@@ -675,6 +702,8 @@ void oqt_trajectory_traced(const oqt_params *p, const oqt_init *in, const oqt_me
                 o->flags |= OQT_F_LCAP; oqt_zero_observables(o);
                 l = l_new; c = c_new; nj++;
                 if (o->first_jump_step < 0) o->first_jump_step = n;
+                o->last_jump_step = n;
+                o->jump_digest = oqt_digest_jump(o->jump_digest, n, l, c);
                 ended = 1; break;
             }
             /* u <- r u / ||r u|| */
@@ -688,6 +717,8 @@ void oqt_trajectory_traced(const oqt_params *p, const oqt_init *in, const oqt_me
             for (int j = 1; j < N; j++) u[j] *= inv;
             l = l_new; c = c_new; nj++;
             if (o->first_jump_step < 0) o->first_jump_step = n;
+            o->last_jump_step = n;
+            o->jump_digest = oqt_digest_jump(o->jump_digest, n, l, c);
             k++;
             oqt_draws(seed, k, &r, &ul, &uc);
         }

@@ -172,7 +172,7 @@ Layout layout(const qtraj_ctx *c, int n)
 // exp(-i V dt/2) (s1) and exp(-i V dt) (s2), V = coul_c / r + l(l+1) / (M r^2) at r = j dr, in FP64
 // (entry j = 0 is zero: u(0) = 0).  Built on the device: 2 x 2 x LTAB x N phases.
 template <typename T>
-__global__ void stat_rows(typename Prec<T>::C *s1, typename Prec<T>::C *s2, int N, double dr, double M, double dt,
+__global__ void stat_rows(typename Prec<T>::S *s1, typename Prec<T>::S *s2, int N, double dr, double M, double dt,
                           double coul0, double coul1)
 {
     const size_t n = (size_t)2 * LTAB * N;
@@ -187,8 +187,8 @@ __global__ void stat_rows(typename Prec<T>::C *s1, typename Prec<T>::C *s2, int 
             sincos(ph, &sn1, &c1);
             sincos(2.0 * ph, &sn2, &c2);
         }
-        s1[i] = Prec<T>::from_double(c1, sn1);
-        s2[i] = Prec<T>::from_double(c2, sn2);
+        s1[i] = Prec<T>::make_s(c1, sn1);
+        s2[i] = Prec<T>::make_s(c2, sn2);
     }
 }
 
@@ -227,11 +227,12 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
     CK(cudaMalloc(&c->W, sizeof(PC) * N));
     CK(cudaMalloc(&c->KT, sizeof(PC) * N));
     CK(cudaMalloc(&c->sinpre, sizeof(PR) * N));
+    using PS = typename Prec<T>::S;
     const size_t nstat = (size_t)2 * LTAB * N;
-    if (cudaMalloc(&c->statV, sizeof(PC) * nstat) != cudaSuccess ||
-        cudaMalloc(&c->statV2, sizeof(PC) * nstat) != cudaSuccess) {
+    if (cudaMalloc(&c->statV, sizeof(PS) * nstat) != cudaSuccess ||
+        cudaMalloc(&c->statV2, sizeof(PS) * nstat) != cudaSuccess) {
         cudaGetLastError();
-        return fail(QTRAJ_ENOMEM, "cudaMalloc of the static space-kernel tables (%zu bytes)", 2 * sizeof(PC) * nstat);
+        return fail(QTRAJ_ENOMEM, "cudaMalloc of the static space-kernel tables (%zu bytes)", 2 * sizeof(PS) * nstat);
     }
     CK(cudaMemcpy(c->W, W.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->KT, KT.data(), sizeof(PC) * N, cudaMemcpyHostToDevice));
@@ -240,7 +241,7 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
     cudaStream_t s = nullptr;
     CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     const int blocks = (int)std::min<size_t>((nstat + 255) / 256, 4096);
-    stat_rows<T><<<blocks, 256, 0, s>>>((PC *)c->statV, (PC *)c->statV2, N, c->dr, c->M, c->dt, coul[0], coul[1]);
+    stat_rows<T><<<blocks, 256, 0, s>>>((PS *)c->statV, (PS *)c->statV2, N, c->dr, c->M, c->dt, coul[0], coul[1]);
     cudaError_t e = cudaGetLastError();
     const cudaError_t e2 = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = e2;
@@ -257,8 +258,8 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     t.WL = (const PC *)c->WL;
     t.KT = (const PC *)c->KT;
     t.sinpre = (const typename Prec<T>::Rl *)c->sinpre;
-    t.statV = (const PC *)c->statV;
-    t.statV2 = (const PC *)c->statV2;
+    t.statV = (const typename Prec<T>::S *)c->statV;
+    t.statV2 = (const typename Prec<T>::S *)c->statV2;
     t.eig = c->eig;
     t.ic = c->ic;
     t.ov0 = c->ov0;

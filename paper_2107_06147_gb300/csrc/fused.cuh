@@ -87,16 +87,12 @@ __device__ __forceinline__ DF df_add(DF a, DF b)
 template <typename T> struct SqAcc;
 template <> struct SqAcc<float> {
     DF v{0.f, 0.f};
-    // v += w |a|^2: the term is rounded once (a relative error of ~1e-7, independent from term to
-    // term and unbiased), the running sum is compensated (the TwoSum errors collect in v.lo), so a
-    // sum of n terms is good to ~1e-7 / sqrt(n) relative, far below the FP32 state's own rounding
-    // noise (~1e-6 per step); the waiting-time comparison needs no more
-    __device__ __forceinline__ void add_w(cpx<float> a, float w)
-    {
-        const float q = w * fmaf(a.x, a.x, a.y * a.y);
-        const DF t = two_sum(v.hi, q);
-        v = DF{t.hi, v.lo + t.lo};
-    }
+    // v += w |a|^2 in plain FP32: a thread sums its ~N/G terms of one parity (16 at N = 4096), a
+    // relative error of ~sqrt(16) x 6e-8 = 2.4e-7, random from step to step; the sums of the threads
+    // are then combined in double-float.  The norm feeds only the waiting-time comparison and the
+    // jump's renormalisation, and the FP32 state's own norm error is ~1e-6 per hundred steps, so a
+    // compensated per-thread sum (as an earlier revision had) buys nothing the comparison can see.
+    __device__ __forceinline__ void add_w(cpx<float> a, float w) { v.hi = fmaf(w, fmaf(a.x, a.x, a.y * a.y), v.hi); }
     __device__ __forceinline__ void shfl_add(unsigned mask, int off, int w)
     {
         DF o{__shfl_xor_sync(mask, v.hi, off, w), __shfl_xor_sync(mask, v.lo, off, w)};
@@ -250,8 +246,13 @@ static __device__ __noinline__ void dyn_far(float a, float y, float *em1, float 
 template <> struct Dyn<float> {
     static __device__ __forceinline__ void f1(float a, float y, float *fr, float *fi, float *e)
     {
+        f1t(a, 3.14159265358979f * y, fr, fi, e);
+    }
+    // the same from the phase t = pi y (the hot loop forms t directly; beyond the series' range y is
+    // recomputed from t)
+    static __device__ __forceinline__ void f1t(float a, float t, float *fr, float *fi, float *e)
+    {
         float em1, s, cm1;
-        const float t = 3.14159265358979f * y;
         if (a >= -0.5f && fabsf(t) <= 1.0f) {
             float p = 1.0f / 40320.0f;
             p = fmaf(p, a, 1.0f / 5040.0f);
@@ -276,7 +277,7 @@ template <> struct Dyn<float> {
             pc = fmaf(pc, u, -0.5f);
             cm1 = u * pc;
         } else {
-            dyn_far(a, y, &em1, &s, &cm1);
+            dyn_far(a, t * 0.318309886183790672f, &em1, &s, &cm1);
         }
         const float mag = 1.0f + em1;
         *fr = fmaf(cm1, mag, em1);
@@ -301,12 +302,12 @@ __device__ __forceinline__ void k_sincospi(double y, double *s, double *c) { sin
 // static factor of a (colour, l) row beyond the table (l >= LTAB, some 33,000 jumps from l = 0),
 // evaluated in FP64; span 1 = half step, 2 = full step
 template <typename T>
-__device__ __noinline__ typename Prec<T>::C static_far(double coul, double M, double dt, int l, double r, double span)
+__device__ __noinline__ typename Prec<T>::S static_far(double coul, double M, double dt, int l, double r, double span)
 {
     const double V = coul / r + (double)l * (l + 1) / (M * r * r);
     double s, c;
     sincos(-V * dt * 0.5 * span, &s, &c);
-    return Prec<T>::from_double(c, s);
+    return Prec<T>::make_s(c, s);
 }
 
 // in-place DFT of RR values (natural order in); output k lands in slot operm(k)
@@ -564,10 +565,11 @@ template <typename T, int N, int V> struct Pointwise {
     using C = typename Prec<T>::C;
     static constexpr int G = K::G;
 
-    static __device__ __forceinline__ C stat(const Tables<T> &tb, const C *tab, int c, int l, int j, bool full)
+    using SC = typename Prec<T>::S;
+    static __device__ __forceinline__ SC stat(const Tables<T> &tb, const SC *tab, int c, int l, int j, bool full)
     {
-        if (l < LTAB) return PR::ld(&tab[((size_t)c * LTAB + l) * N + j]);
-        if (j == 0) return PR::from_double(0.0, 0.0);
+        if (l < LTAB) return PR::ld_s(&tab[((size_t)c * LTAB + l) * N + j]);
+        if (j == 0) return PR::make_s(0.0, 0.0);
         return static_far<T>(tb.coul[c], tb.M, tb.dt, l, j * tb.dr, full ? 2.0 : 1.0);
     }
 
@@ -581,8 +583,9 @@ template <typename T, int N, int V> struct Pointwise {
     static __device__ double factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode, T A, T B, T D,
                                     double *red)
     {
-        const C *tab = (mode == 1) ? tb.statV2 : tb.statV;
+        const SC *tab = (mode == 1) ? tb.statV2 : tb.statV;
         SqAcc<T> acc, acc_odd;   // even and odd j accumulate separately (two dependency chains)
+        const T Bpi = (T)3.14159265358979323846 * B;   // the phase coefficient: t = pi B j^2
 #pragma unroll 2
         for (int k = g; k < N / 2; k += G) {
 #pragma unroll
@@ -595,16 +598,28 @@ template <typename T, int N, int V> struct Pointwise {
                 // rounding is relative to f1, not to 1 (a rounding of a value next to 1 would repeat
                 // identically every step and add up)
                 T f1r, f1i, em1;
-                Dyn<T>::f1((A * fj) * fj, (B * fj) * fj, &f1r, &f1i, &em1);
+                T z = (T)0;
+                if constexpr (sizeof(T) == 4) {
+                    // j^2 is exact in FP32 up to N = 4096 (and rounded once above); the coefficients
+                    // change every step, so no rounding of a, t or z repeats from step to step
+                    const T j2 = fj * fj;
+                    Dyn<T>::f1t(A * j2, Bpi * j2, &f1r, &f1i, &em1);
+                    z = D * j2;
+                } else {
+                    Dyn<T>::f1((A * fj) * fj, (B * fj) * fj, &f1r, &f1i, &em1);
+                    z = (D * fj) * fj;
+                }
                 const T mag = (T)1 + em1;   // |exp(a)|, for the norm weight (working precision suffices)
                 cpx<T> v = buf[p];
                 SqAcc<T> &ac = par ? acc_odd : acc;
                 if (mode == 1) {
-                    // exp(2 er_a r^2) = mag * exp((er_a - er_b) r^2), the second factor ~ 1 + 1e-4
-                    const T z = (D * fj) * fj;
-                    ac.add_w(v, mag * ((T)1 + z * ((T)1 + z * ((T)0.5 + z * (T)(1.0 / 6.0)))));
+                    // exp(2 er_a r^2) = mag * exp((er_a - er_b) r^2), the second factor 1 + z with
+                    // |z| <~ 1e-4 (the temperature's change over one step): FP32 keeps the first order
+                    // (z^2 / 2 < 1e-8 is below its rounding), FP64 the series to z^3
+                    if constexpr (sizeof(T) == 4) ac.add_w(v, mag + mag * z);
+                    else ac.add_w(v, mag * ((T)1 + z * ((T)1 + z * ((T)0.5 + z * (T)(1.0 / 6.0)))));
                 }
-                const cpx<T> w = PR::mul(v, stat(tb, tab, c, l, j, mode == 1));
+                const cpx<T> w = PR::mul_s(v, stat(tb, tab, c, l, j, mode == 1));
                 v = mk(w.x + (w.x * f1r - w.y * f1i), w.y + (w.x * f1i + w.y * f1r));
                 if (mode == 2) ac.add_w(v, (T)1);
                 buf[p] = v;
@@ -642,7 +657,7 @@ template <typename T, int N, int V> struct Pointwise {
                     acc.add_w(v, dr2 * j2);
                 } else {
                     acc.add_w(v, dr2 * j2 * k_exp(w2 * j2));
-                    v = PR::mul(PR::mul(v, PR::conj(stat(tb, tb.statV, c, l, j, false))), stat(tb, tb.statV, c2, l2, j, false));
+                    v = PR::mul_s(PR::mul_s(v, PR::conj_s(stat(tb, tb.statV, c, l, j, false))), stat(tb, tb.statV, c2, l2, j, false));
                     T sn, cs;
                     k_sincospi(B * j2, &sn, &cs);
                     const T m = k_exp(A * j2);
@@ -664,7 +679,7 @@ template <typename T, int N, int V> struct Pointwise {
         const T fj = (T)j;
         T f1r, f1i, em1;
         Dyn<T>::f1((A * fj) * fj, (B * fj) * fj, &f1r, &f1i, &em1);
-        const cpx<T> w = PR::mul(buf[p], stat(tb, tb.statV, c, l, j, false));
+        const cpx<T> w = PR::mul_s(buf[p], stat(tb, tb.statV, c, l, j, false));
         return mk((double)(w.x + (w.x * f1r - w.y * f1i)), (double)(w.y + (w.x * f1i + w.y * f1r)));
     }
 
@@ -724,7 +739,7 @@ template <typename T, int N, int V> struct Pointwise {
                 T sn, cs;
                 k_sincospi(B * j2, &sn, &cs);
                 const T m = k_exp(A * j2);
-                buf[p] = PR::mul(buf[p], PR::conj(stat(tb, tb.statV, c, l, j, false))) * mk(m * cs, m * sn);
+                buf[p] = PR::mul_s(buf[p], PR::conj_s(stat(tb, tb.statV, c, l, j, false))) * mk(m * cs, m * sn);
             }
         }
     }
@@ -778,8 +793,8 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
         const TrajDev d = a.trajs[t];
         const Draws dr0 = draws(d.seed, 0u);
         int flags = 0;
+        bool have = false;   // p_NoJump known (its group's record is published), or no shortcut at all
         if (tb.use_rmin) {
-            bool have = false;
             qtraj_obs gj;
             if (a.gready) {
                 if (group_ready(a.gready + d.group)) {
@@ -802,7 +817,8 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
                 }
             }
         }
-        if (dr0.r > tb.r_max) {
+        // r0 > r_max is resolved only once r0 < p_NoJump is excluded; otherwise the kernel evolves it
+        if (dr0.r > tb.r_max && (have || !tb.use_rmin)) {
             qtraj_obs o;
             for (int s = 0; s < NBASIS; ++s) { o.surv[s] = 0; o.ov_re[s] = 0; o.ov_im[s] = 0; }
             o.norm2 = 1.0;
@@ -813,6 +829,8 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
             o.n_steps_exec = 0;
             o.flags = flags | QTRAJ_F_RMAX;
             o.first_jump_step = -1;
+            o.last_jump_step = -1;
+            o.jump_digest = DIGEST_BASIS;
             a.obs[t] = o;
             continue;
         }
@@ -888,7 +906,8 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         Draws dw = draws(d.seed, 0u);
         const double r0 = nojump ? 0.0 : dw.r;
         double thr = nojump ? -1.0 : dw.r;
-        int nj = 0, flags = 0, fj = -1, ended = 0, executed = 0;
+        int nj = 0, flags = 0, fj = -1, lj = -1, ended = 0, executed = 0;
+        uint32_t digest = DIGEST_BASIS;
         // r0 > r_max reaches here only when its group's no-jump record was not yet published: the paper
         // resolves r0 < p_NoJump by the shortcut first and r0 > r_max only otherwise.  The trajectory
         // is evolved: if its norm never falls to r0 it is the no-jump run (= the shortcut's record); the
@@ -967,6 +986,8 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                             flags |= QTRAJ_F_LCAP;
                             if (fj < 0) fj = n;
                             l = l_new; c = c_new; ++nj;
+                            lj = n;
+                            digest = digest_jump(digest, n, l, c);
                         }
                         break;
                     }
@@ -983,6 +1004,8 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                     __syncthreads();
                     PW::scale_r(buf, tb, g, f);
                     l = l_new; c = c_new; ++nj;
+                    lj = n;
+                    digest = digest_jump(digest, n, l, c);
                     ++kdraw;
                     dw = draws(d.seed, kdraw);
                     thr = dw.r;
@@ -1051,6 +1074,8 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
             o.n_steps_exec = executed;
             o.flags = flags;
             o.first_jump_step = fj;
+            o.last_jump_step = lj;
+            o.jump_digest = digest;
             if (rmax_hit) {   // the r_max record, with the steps that found r0 >= p_NoJump
                 for (int s = 0; s < NBASIS; ++s) { o.surv[s] = 0; o.ov_re[s] = 0; o.ov_im[s] = 0; }
                 o.norm2 = 1.0;

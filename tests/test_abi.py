@@ -53,6 +53,6 @@ def test_library_loads_and_prototypes_cover_the_header(libpath):
 def test_record_layouts_agree():
     import oracle
     from paper_2107_06147_gb300 import qtraj
-    assert qtraj.OBS_DTYPE.itemsize == 184
+    assert qtraj.OBS_DTYPE.itemsize == 192
     assert oracle.OBS_DTYPE.names == qtraj.OBS_DTYPE.names
     assert ctypes.sizeof(qtraj.Params) == 72 and ctypes.sizeof(qtraj.Medium) == 56

@@ -7,11 +7,17 @@ conditioned: the oracle run twice on initial states 1e-15 apart ends 1e-14 apart
 jumps, at N = 512 and at the headline N = 4096).  Trajectories flagged borderline
 (|norm^2 - r| < 1e-12 at some comparison) on either side are excluded from the sequence identity.
 FP32 fused form: jump decisions are taken on an FP32 state, so a trajectory whose norm crosses its
-threshold within the FP32 error of the state may jump one step earlier or later; the checks are (i)
-at least 85% identical jump sequences, (ii) on those, survival ratios within 1e-3 relative (to
-max(1, S)) and a median final-state error below 5e-4 relative L2 (times n_jumps/10 above ten jumps),
-and (iii) the paired ensemble means
-of the survival ratios (same seeds on both sides) within 1e-4 absolute.
+threshold within the FP32 error of the state may jump one step earlier or later, after which it is
+another (equally valid) sample of the unravelling.  The checks are (i) the paired ensemble means of
+the survival ratios (same seeds on both sides) within 1e-4 absolute -- the FP32 criterion of the
+task statement; (ii) at least 85% of the trajectories with the oracle's whole jump sequence (equal
+jump digests: every jump at the same step with the same outcome); (iii) on those, every survival
+ratio within FP32_MODEL * sqrt(N * n_steps) relative to max(1, S), and every final state within
+the same bound in relative L2.  (iii) is an error model, not a fitted tolerance: the FP32 state
+carries the rounding noise of the sine transform's odd coefficients, which are running sums of FFT
+outputs, so its relative error grows like sqrt(N) per step and like sqrt(steps) over a medium; the
+largest errors measured on GB300 over N = 64 ... 16384 and 291 ... 11,899 steps are
+(0.4 ... 2) x 5.5e-8 sqrt(N n_steps), and FP32_MODEL is four times that constant.
 """
 import numpy as np
 import pytest
@@ -21,9 +27,13 @@ from conftest import oracle_inputs
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
-FP32_SURV_REL = 1e-3
-FP32_STATE_MEDIAN = 5e-4
+FP32_MODEL = 2.2e-7           # per-trajectory bound / sqrt(N * n_steps), identical jump sequences
+FP32_SURV_REL = 1e-3          # end-of-step norms of capped trajectories (test_caps)
 FP32_ENSEMBLE_ABS = 1e-4
+
+
+def fp32_bound(N, n_steps):
+    return FP32_MODEL * np.sqrt(N * np.maximum(n_steps, 1))
 
 
 @pytest.fixture(scope="module")
@@ -76,7 +86,7 @@ def same_bookkeeping(q, obs, ref, ok):
     """Jump sequence, quantum numbers, executed steps and flags equal on the trajectories `ok`, up to
     the lazy shortcut and the borderline flag."""
     lazy = lazy_shortcut(q, obs, ref)
-    for f in ("n_jumps", "first_jump_step", "l", "color"):
+    for f in ("n_jumps", "first_jump_step", "last_jump_step", "jump_digest", "l", "color"):
         assert np.array_equal(obs[f][ok], ref[f][ok]), (f, obs[f][ok], ref[f][ok])
     assert np.array_equal(obs["n_steps_exec"][ok & ~lazy], ref["n_steps_exec"][ok & ~lazy])
     assert (obs["n_jumps"][ok & lazy] == 0).all() and (obs["first_jump_step"][ok & lazy] == -1).all()
@@ -104,18 +114,20 @@ def check_fp64(q, obs, ref, u, uref):
 
 def check_fp32(q, obs, ref, u, uref, min_same=0.85):
     assert np.array_equal(obs["r0"], ref["r0"])
-    same = (obs["n_jumps"] == ref["n_jumps"]) & (obs["first_jump_step"] == ref["first_jump_step"]) & \
+    N = u.shape[1]
+    dm = np.abs(obs["surv"].mean(axis=0) - ref["surv"].mean(axis=0))
+    assert dm.max() <= FP32_ENSEMBLE_ABS, dm
+    same = (obs["jump_digest"] == ref["jump_digest"]) & (obs["n_jumps"] == ref["n_jumps"]) & \
            (obs["l"] == ref["l"]) & (obs["color"] == ref["color"])
     assert same.mean() >= min_same, same.mean()
-    rel = np.abs(obs["surv"][same] - ref["surv"][same]) / np.maximum(1.0, np.abs(ref["surv"][same]))
-    assert rel.max() <= FP32_SURV_REL, rel.max()
+    steps = np.maximum(obs["n_steps_exec"], ref["n_steps_exec"])
+    bound = fp32_bound(N, steps)
+    rel = np.abs(obs["surv"] - ref["surv"]).max(axis=1) / np.maximum(1.0, np.abs(ref["surv"]).max(axis=1))
+    assert (rel[same] <= bound[same]).all(), (rel[same] / bound[same]).max()
     ran = same & (ref["n_steps_exec"] > 0) & (obs["n_steps_exec"] > 0) & ((ref["flags"] & (q.F_LCAP | q.F_MAXJUMPS)) == 0)
     if ran.any():
         du = np.linalg.norm(u[ran] - uref[ran], axis=1) / np.linalg.norm(uref[ran], axis=1)
-        du = du / np.maximum(1.0, ref["n_jumps"][ran] / 10.0)     # the jumps' magnification, as for FP64
-        assert np.median(du) < FP32_STATE_MEDIAN, np.median(du)
-    dm = np.abs(obs["surv"].mean(axis=0) - ref["surv"].mean(axis=0))
-    assert dm.max() <= FP32_ENSEMBLE_ABS, dm
+        assert (du <= bound[ran]).all(), (du / bound[ran]).max()
 
 
 # ------------------------------------------------------------------------------------------------
@@ -224,19 +236,21 @@ def test_caps(q, opt, precision):
         if precision == 0:
             check_fp64(q, obs, ref, u, uref)
         else:
-            # ~11,000 steps: FP32 rounding moves a jump by a step or two, so the FP32 criterion is the
-            # same jump count, l and colour with the first jump within 3 steps, and the end-of-step norm
-            # of a capped trajectory where it stopped at the same step
-            near = (obs["n_jumps"] == ref["n_jumps"]) & (obs["l"] == ref["l"]) & (obs["color"] == ref["color"]) & \
-                   (np.abs(obs["first_jump_step"] - ref["first_jump_step"]) <= 3)
-            assert near.mean() >= 0.85, near.mean()
-            cap = (ref["flags"] & (q.F_MAXJUMPS | q.F_LCAP)) != 0
-            same = cap & near & (obs["flags"] == ref["flags"]) & (obs["n_steps_exec"] == ref["n_steps_exec"])
-            if same.any():
-                dn = np.abs(obs["norm2"][same] / ref["norm2"][same] - 1)
-                assert dn.max() < FP32_SURV_REL, dn.max()
-            dm = np.abs(obs["surv"].mean(axis=0) - ref["surv"].mean(axis=0))
-            assert dm.max() <= FP32_ENSEMBLE_ABS * 10, dm
+            # ~11,000 steps: FP32 rounding may move a jump, after which the capped/uncapped outcome of a
+            # 32-trajectory batch can flip, so the ensemble of this small batch is no test; the checks
+            # are the fraction of identical jump sequences and, on those, the records and the
+            # end-of-step norms of the capped trajectories within the FP32 error model
+            same = (obs["jump_digest"] == ref["jump_digest"]) & (obs["n_jumps"] == ref["n_jumps"]) & \
+                   (obs["l"] == ref["l"]) & (obs["color"] == ref["color"])
+            assert same.mean() >= 0.85, same.mean()
+            assert np.array_equal(obs["flags"][same] & ~q.F_BORDERLINE, ref["flags"][same] & ~q.F_BORDERLINE)
+            assert np.array_equal(obs["n_steps_exec"][same], ref["n_steps_exec"][same])
+            cap = same & ((ref["flags"] & (q.F_MAXJUMPS | q.F_LCAP)) != 0)
+            assert cap.any()
+            dn = np.abs(obs["norm2"][cap] / ref["norm2"][cap] - 1)
+            assert (dn <= fp32_bound(64, ref["n_steps_exec"][cap])).all(), dn.max()
+            rel = np.abs(obs["surv"][same] - ref["surv"][same]).max(axis=1)
+            assert (rel <= fp32_bound(64, ref["n_steps_exec"][same]) * np.maximum(1, ref["surv"][same].max(1))).all()
 
 
 @pytest.mark.parametrize("form,precision", [(0, 0), (1, 0), (0, 1)])
@@ -619,13 +633,15 @@ def test_uneven_batch_against_oracle(q, precision):
     assert len(set(ref["n_steps_exec"])) > 10 and (ref["n_jumps"] > 0).sum() >= 5   # uneven lifetimes, jumps
     if precision == 0:
         ok = ((obs["flags"] | ref["flags"]) & q.F_BORDERLINE) == 0
-        for f in ("n_jumps", "first_jump_step", "l", "color", "n_steps_exec"):
+        for f in ("n_jumps", "first_jump_step", "last_jump_step", "jump_digest", "l", "color", "n_steps_exec"):
             assert np.array_equal(obs[f][ok], ref[f][ok]), f
-        np.testing.assert_allclose(obs["surv"][ok], ref["surv"][ok], rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(obs["surv"][ok], ref["surv"][ok], rtol=1e-10, atol=1e-14)
     else:
-        same = (obs["n_jumps"] == ref["n_jumps"]) & (obs["first_jump_step"] == ref["first_jump_step"])
-        assert same.mean() >= 0.8
+        same = (obs["jump_digest"] == ref["jump_digest"]) & (obs["n_jumps"] == ref["n_jumps"])
+        assert same.mean() >= 0.85
         assert np.abs(obs["surv"].mean(0) - ref["surv"].mean(0)).max() <= FP32_ENSEMBLE_ABS
+        rel = np.abs(obs["surv"][same] - ref["surv"][same]).max(axis=1) / np.maximum(1, ref["surv"][same].max(1))
+        assert (rel <= fp32_bound(u["N"][same], ref["n_steps_exec"][same])).all()
 
 
 @pytest.mark.parametrize("precision,form", [(0, 0), (1, 0), (0, 1)])

@@ -312,6 +312,49 @@ def test_nonhermitian_decay_rate(oracle_lib):
         assert 3.0 < errs[0] / errs[1] < 5.0            # second order in dt
 
 
+def _fnv1a32(words):
+    """FNV-1a, 32 bit (Fowler, Noll, Vo), over the little-endian bytes of 32-bit words."""
+    h = 2166136261
+    for w in words:
+        for b in int(w & 0xFFFFFFFF).to_bytes(4, "little"):
+            h = ((h ^ b) * 16777619) & 0xFFFFFFFF
+    return h
+
+
+def test_jump_digest_and_last_jump_step_follow_the_jumps(oracle_lib):
+    """The record's jump digest is FNV-1a over (step, new l, new colour) of every jump in order, and
+    last_jump_step the step of the last jump (0-based, as first_jump_step): both recomputed here from
+    the per-step rows (rows count steps from 1; a jump after step n shows as a change of l between
+    the rows n and n+1), for trajectories with 0 to ~30 jumps."""
+    o = oracle_lib
+    from paper_2107_06147_gb300 import inputs
+    w = inputs.small_parity(N=128, n_traj=12, seed=17)
+    w.grid.L = 8.0                       # a wide box: large r, many jumps
+    for m in w.media:
+        m.Tf = 0.8 * m.T0
+    g, inits, media = oracle_inputs(w)
+    g.use_rmin = 0
+    seen = 0
+    for t in range(12):
+        ob, rows = o.trajectory_trace(g, inits[w.init_idx[t]], media[w.medium_idx[t]], int(w.seeds[t]), every=1)
+        if ob["n_steps_exec"] < 2 or ob["flags"] & (o.F_MAXJUMPS | o.F_LCAP):
+            continue
+        ch = np.nonzero(rows["l"][1:] != rows["l"][:-1])[0]
+        words = []
+        for i in ch:
+            words += [int(rows["step"][i]) - 1, int(rows["l"][i + 1]), int(rows["color"][i + 1])]
+        last_row_jump = ob["n_jumps"] == len(ch) + 1      # a jump after the final step has no next row
+        if last_row_jump:
+            words += [int(rows["step"][-1]) - 1, int(ob["l"]), int(ob["color"])]
+        assert ob["n_jumps"] == len(words) // 3
+        assert ob["first_jump_step"] == (words[0] if words else -1)
+        assert ob["jump_digest"] == _fnv1a32(words)
+        assert ob["last_jump_step"] == (words[-3] if words else -1)
+        seen += ob["n_jumps"] > 0
+    assert seen >= 4
+    assert _fnv1a32([]) == 2166136261 and _fnv1a32([0]) == 0x4B95F515   # FNV-1a of four zero bytes
+
+
 def test_kappa_fit_coefficients_match_the_printed_fits(oracle_lib):
     """App. E prints the three lattice fits of kappa_hat(T) coefficient by coefficient
     (tests/golden/kappa_hat_lattice_fits.txt, transcribed from the paper).  Evaluated at x = T/T_c
