@@ -211,6 +211,63 @@ template <typename T, int G> __device__ __forceinline__ double slot_norm(SqAcc<T
     }
 }
 
+// The norm sum as the step loop compares it with the waiting-time threshold: double-float in the FP32
+// forms (so that no FP64 instruction -- a slow pipe on GB300 -- runs in every step), double in FP64.
+template <typename T> struct NormSum { using type = double; };
+template <> struct NormSum<float> { using type = DF; };
+
+template <typename T, int G> __device__ __forceinline__ typename NormSum<T>::type slot_norm_sum(SqAcc<T> acc, double *red)
+{
+    if constexpr (sizeof(T) == 4) {
+        constexpr int W = G < 32 ? G : 32;
+        const unsigned mask = lane_mask<G>();
+#pragma unroll
+        for (int off = W / 2; off > 0; off >>= 1) acc.shfl_add(mask, off, W);
+        DF v = acc.v;
+        if constexpr (G <= 32) {
+            v.hi = __shfl_sync(mask, v.hi, 0, W);
+            v.lo = __shfl_sync(mask, v.lo, 0, W);
+        } else {
+            DF *fr = reinterpret_cast<DF *>(red);
+            if ((threadIdx.x & 31) == 0) fr[threadIdx.x >> 5] = v;
+            __syncthreads();
+            v = fr[0];
+#pragma unroll
+            for (int w = 1; w < G / 32; ++w) v = df_add(v, fr[w]);
+            __syncthreads();
+        }
+        return v;
+    } else {
+        return slot_norm<T, G>(acc, red);
+    }
+}
+
+// The waiting-time threshold in the form of the norm sum it is compared with: r / dr (the norm is
+// dr times the sum), as a normalised double-float in FP32 forms, computed in FP64 once per waiting
+// period.  The comparisons are then exact on the double-float values.
+template <typename T> struct Threshold;
+template <> struct Threshold<double> {
+    double thr, dr;
+    __device__ void set(double r, double dr_) { thr = r; dr = dr_; }
+    __device__ bool finite(double s) const { return isfinite(s * dr); }
+    __device__ bool reached(double s) const { return s * dr <= thr; }
+    __device__ bool near(double s, double eps) const { return fabs(s * dr - thr) < eps; }
+};
+template <> struct Threshold<float> {
+    DF t;
+    float eps_s;
+    __device__ void set(double r, double dr)
+    {
+        const double q = r / dr;
+        t.hi = (float)q;
+        t.lo = (float)(q - (double)t.hi);
+        eps_s = (float)(border_eps<float>() / dr);
+    }
+    __device__ bool finite(DF s) const { return isfinite(s.hi) && isfinite(s.lo); }
+    __device__ bool reached(DF s) const { return s.hi < t.hi || (s.hi == t.hi && s.lo <= t.lo); }
+    __device__ bool near(DF s, double) const { return fabsf((s.hi - t.hi) + (s.lo - t.lo)) < eps_s; }
+};
+
 // exp(x) and (cos, sin)(pi y): the pi-scaled form has no large-argument reduction path
 __device__ __forceinline__ float k_exp(float x) { return expf(x); }
 __device__ __forceinline__ double k_exp(double x) { return exp(x); }
@@ -580,8 +637,8 @@ template <typename T, int N, int V> struct Pointwise {
     // coefficients times dr^2 (phase / pi): A for the magnitude, B for the phase, D = (er_a - er_b) dr^2
     // for the norm weight; they are rounded once per step and multiply the exact j twice, so no
     // rounding that repeats identically every step enters the arguments.
-    static __device__ double factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode, T A, T B, T D,
-                                    double *red)
+    static __device__ typename NormSum<T>::type factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode,
+                                                       T A, T B, T D, double *red)
     {
         const SC *tab = (mode == 1) ? tb.statV2 : tb.statV;
         SqAcc<T> acc, acc_odd;   // even and odd j accumulate separately (two dependency chains)
@@ -625,9 +682,9 @@ template <typename T, int N, int V> struct Pointwise {
                 buf[p] = v;
             }
         }
-        if (mode == 0) return 0.0;
+        if (mode == 0) return {};
         acc.merge(acc_odd);
-        return slot_norm<T, G>(acc, red);
+        return slot_norm_sum<T, G>(acc, red);
     }
 
     static __device__ cpx<double> to_d(const typename Prec<double>::C &a) { return a; }
@@ -839,13 +896,13 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
 }
 
 // Occupancy target of a kernel variant: variant 0 asks for 512 resident threads per SM in FP32
-// (<= 128 registers), except at N = 4096 where 384 (3 CTAs of 128 threads, <= 168 registers, fewer
-// spills) measured 4.5% faster on GB300 (at N = 1024, 2048 and 8192 the same change lost 3-25%);
+// (<= 128 registers; at N = 4096 four CTAs of 128 threads, measured 8% faster on GB300 than three at
+// <= 168 registers once the static tables lost their low parts and the norm sums their compensation);
 // variant 1 asks for 640 (<= 102 registers, at the price of more spills), variants 2 and 3 (radix 8)
 // for 768 and 1024.  FP64 holds twice the state and takes what the compiler needs.
 template <typename T, int N, int V> struct FusedBounds {
     static constexpr int G = FusedPlan<N, V>::G;
-    static constexpr int THREADS = (V == 0 || V == 4) ? (N == 4096 ? 384 : 512) : V == 1 ? 640 : V == 2 ? 768 : 1024;
+    static constexpr int THREADS = (V == 0 || V == 4) ? 512 : V == 1 ? 640 : V == 2 ? 768 : 1024;
     static constexpr int MB = THREADS / G > 32 ? 32 : (THREADS / G > 0 ? THREADS / G : 1);
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? MB : 1;
 };
@@ -905,7 +962,8 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         uint32_t kdraw = 0;
         Draws dw = draws(d.seed, 0u);
         const double r0 = nojump ? 0.0 : dw.r;
-        double thr = nojump ? -1.0 : dw.r;
+        Threshold<T> thr;
+        thr.set(nojump ? -1.0 : dw.r, dr);
         int nj = 0, flags = 0, fj = -1, lj = -1, ended = 0, executed = 0;
         uint32_t digest = DIGEST_BASIS;
         // r0 > r_max reaches here only when its group's no-jump record was not yet published: the paper
@@ -953,22 +1011,23 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                 }
             }
             const T Tsum = last ? T3a : T3a + T3b, Ksum = last ? K3a : K3a + K3b;
-            const double n2 = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Ksum, eij * Tsum,
-                                         last ? (T)0 : erj * (K3a - K3b), red) * dr;
-            if (!isfinite(n2)) {
+            const auto n2s = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Ksum, eij * Tsum,
+                                        last ? (T)0 : erj * (K3a - K3b), red);   // norm^2 / dr
+            if (!thr.finite(n2s)) {
                 flags |= QTRAJ_F_NONFINITE;
                 ended = 1;
                 if (g == 0) atomicOr(a.status, 1);
                 break;
             }
             if (!nojump) {
-                if (fabs(n2 - thr) < border_eps<T>()) flags |= QTRAJ_F_BORDERLINE;
-                if (n2 <= thr && rmax_pending) {
+                if (thr.near(n2s, border_eps<T>())) flags |= QTRAJ_F_BORDERLINE;
+                const bool trig = thr.reached(n2s);
+                if (trig && rmax_pending) {
                     rmax_hit = true;
                     ended = 1;
                     break;
                 }
-                if (n2 <= thr) {
+                if (trig) {
                     // a trajectory stopped by a cap keeps its end-of-step state
                     const bool cap_j = tb.max_jumps >= 0 && nj >= tb.max_jumps;
                     const int l_new = (dw.ul < (double)l / (2.0 * l + 1.0)) ? l - 1 : l + 1;
@@ -1008,7 +1067,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                     digest = digest_jump(digest, n, l, c);
                     ++kdraw;
                     dw = draws(d.seed, kdraw);
-                    thr = dw.r;
+                    thr.set(dw.r, dr);
                 }
             }
         }
