@@ -37,7 +37,8 @@ class Params(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_double), ("dt", C.c_double), ("M", C.c_double),
                 ("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int),
                 ("max_jumps", C.c_int), ("r_max", C.c_double), ("l_cap", C.c_int),
-                ("use_rmin", C.c_int), ("t_vac", C.c_double), ("basis", C.POINTER(C.c_double))]
+                ("use_rmin", C.c_int), ("t_vac", C.c_double), ("basis", C.POINTER(C.c_double)),
+                ("potential", C.c_int), ("ksu_fmd", C.c_double)]
 
 
 class Init(C.Structure):
@@ -120,6 +121,13 @@ def lib():
                                             C.POINTER(C.c_int)]
         L.oqt_kappa_fit.argtypes = [C.c_int, C.c_double]
         L.oqt_kappa_fit.restype = C.c_double
+        for f in ("oqt_expE1", "oqt_expmEi", "oqt_ksu_phi"):
+            getattr(L, f).argtypes = [C.c_double]
+            getattr(L, f).restype = C.c_double
+        L.oqt_alpha_s_run.argtypes = [C.c_double, C.c_double]
+        L.oqt_alpha_s_run.restype = C.c_double
+        L.oqt_ksu_debye_mass.argtypes = [C.POINTER(Params), C.c_double]
+        L.oqt_ksu_debye_mass.restype = C.c_double
         _lib = L
     return _lib
 
@@ -147,6 +155,8 @@ class Grid:
     use_rmin: int = 1
     t_vac: float = 0.0
     basis: object = None          # (NBASIS, N) overlap basis (numerical eigenstates); None: analytic
+    potential: int = 0            # 0: App. E OQS+pNRQCD with jumps; 1: isotropic KSU (no jumps)
+    ksu_fmd: float = 1.0          # F_mD of the KSU Debye mass
 
     def c(self) -> Params:
         b = None
@@ -154,7 +164,8 @@ class Grid:
             self._basis_c = np.ascontiguousarray(self.basis, dtype=np.float64)
             b = _dp(self._basis_c)
         return Params(self.N, self.L, self.dt, self.M, self.alpha_s, self.Nc, self.deriv_type,
-                      self.max_jumps, self.r_max, self.l_cap, self.use_rmin, self.t_vac, b)
+                      self.max_jumps, self.r_max, self.l_cap, self.use_rmin, self.t_vac, b, self.potential,
+                      self.ksu_fmd)
 
 
 def init_spec(kind: str = "gauss", width: float = 0.2, n: int = 1, l: int = 0, color: int = 0) -> Init:
@@ -323,6 +334,38 @@ def trajectory_trace(g: Grid, spec: Init, m: Medium, seed: int, every: int, cap:
     lib().oqt_trajectory_traced(C.byref(p), C.byref(spec), C.byref(m), C.c_uint64(seed), None, C.byref(o), None,
                                 every, C.c_void_p(rec.ctypes.data), cap, C.byref(n))
     return np.frombuffer(bytes(o), dtype=OBS_DTYPE).copy()[0], rec[: n.value].copy()
+
+
+def expE1(x: float) -> float:
+    """e^x E1(x) for x > 0 (the oracle's own evaluation)."""
+    return lib().oqt_expE1(x)
+
+
+def expmEi(x: float) -> float:
+    """e^-x Ei(x) for x > 0 (the oracle's own evaluation)."""
+    return lib().oqt_expmEi(x)
+
+
+def ksu_phi(rhat: float) -> float:
+    """phi(rhat) of the isotropic KSU potential's imaginary part (App. E)."""
+    return lib().oqt_ksu_phi(rhat)
+
+
+def alpha_s_run(mu: float, Nc: float = 3.0) -> float:
+    """The one-loop running coupling from alpha_s(5 GeV) = 0.2034 (N_F = 3)."""
+    return lib().oqt_alpha_s_run(mu, Nc)
+
+
+def ksu_debye_mass(g: Grid, T: float) -> float:
+    p = g.c()
+    return lib().oqt_ksu_debye_mass(C.byref(p), T)
+
+
+def ksu_potential(g: Grid, l: int, T: float, r: float) -> complex:
+    """The KSU potential V_R + i V_I + l(l+1)/(M r^2) at temperature T (GeV) and r (GeV^-1)."""
+    h = Grid(**{k: getattr(g, k) for k in g.__dataclass_fields__})
+    h.potential = 1
+    return potential(h, 0, l, T ** 3, 0.0, 0.0, r)
 
 
 def kappa_fit(which: int, T: float) -> float:

@@ -62,6 +62,9 @@ typedef struct {
     int use_rmin;     /* 1: rMin shortcut */
     double t_vac;     /* vacuum evolution before the medium, GeV^-1 (Table 1: tmed - t0); 0: none */
     const double *basis; /* OQT_NBASIS x N overlap basis (numerical eigenstates), NULL: analytic Coulomb */
+    int potential;    /* 0: the OQS+pNRQCD potential of App. E with jumps; 1: the isotropic KSU
+                         potential of App. E (singlet, H_eff only, no jumps) */
+    double ksu_fmd;   /* F_mD, the KSU Debye-mass factor */
 } oqt_params;
 
 /* kind 0 Gaussian, 1 analytic Coulomb eigenstate, 2 a given (numerical) eigenstate in u0 (N values,
@@ -288,6 +291,119 @@ double oqt_kappa_at(const oqt_medium *m, double T3)
     return oqt_kappa_fit((int)(-m->kappa_hat), cbrt(T3));
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* The isotropic KSU potential (App. E, "Isotropic KSU potential"): a Karsch-Mehr-Satz real part  */
+/* capped at the vacuum Cornell potential's string-breaking value, and the leading-order          */
+/* imaginary part of the chromoelectric screening regime.  Constants as printed: a = 0.409,       */
+/* sigma = 0.21 GeV^2, r_SB = 1.25 fm, alpha_s(5 GeV) = 0.2034.  Readings (the paper leaves them    */
+/* open): alpha_s(mu) runs at one loop from alpha_s(5 GeV) with N_F = 3 flavours, which also enter */
+/* m_D; the alpha_s of V_I is the same alpha_s(2 pi T); C_F = (Nc^2-1)/(2 Nc) (4/3 at Nc = 3).      */
+/* ------------------------------------------------------------------------------------------ */
+#define OQT_KSU_A 0.409
+#define OQT_KSU_SIGMA 0.21
+#define OQT_KSU_RSB_FM 1.25
+#define OQT_KSU_ALPHAS_MZ 0.2034   /* at mu0 = 5 GeV */
+#define OQT_KSU_MU0 5.0
+#define OQT_KSU_NF 3
+#define OQT_EULER_GAMMA 0.57721566490153286061
+
+/* one-loop running coupling: alpha_s(mu) = alpha_0 / (1 + alpha_0 b0 ln(mu^2/mu0^2)),
+ * b0 = (11 Nc - 2 N_F) / (12 pi) */
+double oqt_alpha_s_run(double mu, double Nc)
+{
+    double b0 = (11.0 * Nc - 2.0 * OQT_KSU_NF) / (12.0 * OQT_PI);
+    return OQT_KSU_ALPHAS_MZ / (1.0 + OQT_KSU_ALPHAS_MZ * b0 * log(mu * mu / (OQT_KSU_MU0 * OQT_KSU_MU0)));
+}
+
+/* the isotropic Debye mass m_D = F_mD T sqrt(Nc (1 + N_F/6) pi alpha), alpha = C_F alpha_s(2 pi T) */
+double oqt_ksu_debye_mass(const oqt_params *p, double T)
+{
+    if (T <= 0) return 0.0;
+    double alpha = oqt_CF(p->Nc) * oqt_alpha_s_run(2.0 * OQT_PI * T, p->Nc);
+    return p->ksu_fmd * T * sqrt(p->Nc * (1.0 + OQT_KSU_NF / 6.0) * OQT_PI * alpha);
+}
+
+/* E1(x) = int_x^inf e^-t / t dt for x > 0, times e^x: the power series of E1 (x <= 1) or the
+ * continued fraction e^x E1(x) = 1/(x+1- 1/(x+3- 4/(x+5- 9/(x+7- ...)))) (x > 1), evaluated by
+ * the modified Lentz method */
+double oqt_expE1(double x)
+{
+    if (x <= 1.0) {
+        double sum = 0.0, term = 1.0;
+        for (int k = 1; k < 60; k++) {
+            term *= -x / k;
+            sum += term / k;
+        }
+        return exp(x) * (-OQT_EULER_GAMMA - log(x) - sum);
+    }
+    double b = x + 1.0, c = 1e300, d = 1.0 / b, h = d;
+    for (int i = 1; i < 1000; i++) {
+        double an = -(double)i * i;
+        b += 2.0;
+        d = 1.0 / (an * d + b);
+        c = b + an / c;
+        double del = c * d;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-17) break;
+    }
+    return h;
+}
+
+/* Ei(x) = PV int_-inf^x e^t / t dt for x > 0, times e^-x: the power series
+ * Ei(x) = gamma + ln x + sum_k x^k / (k k!) (all terms positive) for x <= 60, the asymptotic series
+ * e^-x Ei(x) ~ sum_k k!/x^(k+1), cut before its terms grow, above (its error ~ e^-x) */
+double oqt_expmEi(double x)
+{
+    if (x <= 60.0) {
+        double sum = 0.0, term = 1.0;
+        for (int k = 1; k < 400; k++) {
+            term *= x / k;
+            double t = term / k;
+            sum += t;
+            if (t < 1e-18 * sum) break;
+        }
+        return exp(-x) * (OQT_EULER_GAMMA + log(x) + sum);
+    }
+    double sum = 0.0, term = 1.0 / x, prev = 1e300;
+    for (int k = 0; k < 200; k++) {
+        if (term > prev) break;
+        sum += term;
+        prev = term;
+        term *= (k + 1.0) / x;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+/* phi(rhat) = 2 int_0^inf dz z/(z^2+1)^2 [1 - sin(z rhat)/(z rhat)] (the V_I of the isotropic KSU
+ * potential): with int_0^inf sin(a z)/(1+z^2)^2 dz = [(1+a) e^-a Ei(a) + (1-a) e^a E1(a)]/4 (the
+ * derivative in b at b = 1 of int sin(a z)/(b^2+z^2) dz = [e^-ab Ei(ab) - e^ab Ei(-ab)]/(2b), and
+ * 2 int z/(z^2+1)^2 dz = 1), phi(a) = 1 - [(1+a) e^-a Ei(a) + (1-a) e^a E1(a)] / (2a); phi(0) = 0. */
+double oqt_ksu_phi(double a)
+{
+    if (a <= 0) return 0.0;
+    return 1.0 - ((1.0 + a) * oqt_expmEi(a) + (1.0 - a) * oqt_expE1(a)) / (2.0 * a);
+}
+
+/* the KSU potential at r (singlet, angular momentum l) and temperature T: V_R + i V_I + l(l+1)/(M r^2) */
+double complex oqt_ksu_potential(const oqt_params *p, int l, double T, double r)
+{
+    const double a = OQT_KSU_A, sig = OQT_KSU_SIGMA, rsb = OQT_KSU_RSB_FM / OQT_HBARC;
+    double vcap = -a / rsb + sig * rsb;           /* V_vac(r_SB) */
+    double re, im = 0.0;
+    double mD = oqt_ksu_debye_mass(p, T);
+    if (mD <= 0) {                                 /* vacuum: the Cornell potential with string breaking */
+        re = r <= rsb ? -a / r + sig * r : vcap;
+    } else {
+        double e = exp(-mD * r);
+        double kms = -a / r * (1.0 + mD * r) * e + 2.0 * sig / mD * (1.0 - e) - sig * r * e;
+        re = kms <= vcap ? kms : vcap;
+        im = -oqt_alpha_s_run(2.0 * OQT_PI * T, p->Nc) * oqt_CF(p->Nc) * T * oqt_ksu_phi(mD * r);
+    }
+    re += (double)l * (l + 1) / (p->M * r * r);
+    return re + I * im;
+}
+
 /* V_eff(r) for colour c (0 singlet, 1 octet), angular momentum l, temperature cubed T3.
  * singlet: -C_F a_s/r + gam T^3 r^2/2 - i kap T^3 r^2/2
  * octet  : +a_s/(2 Nc r) + f gam T^3 r^2 - i f kap T^3 r^2,  f = (Nc^2-2)/(4(Nc^2-1)) = 7/32
@@ -295,6 +411,7 @@ double oqt_kappa_at(const oqt_medium *m, double T3)
 double complex oqt_potential(const oqt_params *p, int color, int l, double T3, double kappa_hat,
                              double gamma_hat, double r)
 {
+    if (p->potential == 1) return oqt_ksu_potential(p, l, cbrt(T3), r);
     double Nc = p->Nc, coul, f;
     if (color == 0) { coul = -oqt_CF(Nc) * p->alpha_s / r; f = 0.5; }
     else { coul = p->alpha_s / (2.0 * Nc * r); f = (Nc * Nc - 2.0) / (4.0 * (Nc * Nc - 1.0)); }
@@ -564,7 +681,9 @@ static void oqt_finalize(const oqt_params *p, const oqt_basis *b, const double c
         for (int j = 1; j < N; j++) ov += b->phi[(size_t)s * N + j] * u[j];
         ov *= dr;
         o->ov_re[s] = creal(ov); o->ov_im[s] = cimag(ov);
-        double prob = (creal(ov) * creal(ov) + cimag(ov) * cimag(ov)) / n2;
+        /* with jumps the ensemble estimator takes the normalised state; the KSU evolution has no
+         * jumps, so the norm it loses is the dissociation and the overlap is taken unnormalised */
+        double prob = (creal(ov) * creal(ov) + cimag(ov) * cimag(ov)) / (p->potential == 1 ? 1.0 : n2);
         if (b->ov0_zero[s]) o->surv[s] = prob;
         else {
             double d = creal(b->ov0[s]) * creal(b->ov0[s]) + cimag(b->ov0[s]) * cimag(b->ov0[s]);
@@ -649,11 +768,13 @@ void oqt_trajectory_traced(const oqt_params *p, const oqt_init *in, const oqt_me
     double r, ul, uc;
     oqt_draws(seed, k, &r, &ul, &uc);
     o->r0 = r;
+    const int no_jumps = p->potential == 1;   /* the KSU potentials have no jump operators */
+    if (no_jumps) { r = -1.0; o->r0 = 0.0; }
     o->l = in->l; o->color = in->color;
     double complex *u = malloc(sizeof(double complex) * N);
     oqt_start_state(p, in, u);
 
-    if (p->use_rmin && nojump) {
+    if (p->use_rmin && nojump && !no_jumps) {
         if (fabs(r - nojump->norm2) < OQT_BORDERLINE_EPS) o->flags |= OQT_F_BORDERLINE;
         if (r < nojump->norm2) {   /* no jump can happen: the norm never increases */
             double r0 = o->r0;
@@ -667,7 +788,7 @@ void oqt_trajectory_traced(const oqt_params *p, const oqt_init *in, const oqt_me
             return;
         }
     }
-    if (r > p->r_max) {
+    if (!no_jumps && r > p->r_max) {
         oqt_zero_observables(o);
         o->flags |= OQT_F_RMAX;
         o->norm2 = 1.0;

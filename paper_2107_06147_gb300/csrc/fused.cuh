@@ -291,6 +291,7 @@ template <typename T> __device__ __noinline__ T table_T3_far(const double *p, in
 // FP64: exp and sincospi; a rounding next to 1 is 1e-16 there and does not matter.
 template <typename T> struct Dyn;
 // the rare points outside the series' ranges, kept out of line so the hot loop stays small
+static __device__ __noinline__ float em1_far(float a) { return expf(a) - 1.0f; }
 static __device__ __noinline__ void dyn_far(float a, float y, float *em1, float *s, float *cm1)
 {
     *em1 = expf(a) - 1.0f;
@@ -304,6 +305,22 @@ template <> struct Dyn<float> {
     static __device__ __forceinline__ void f1(float a, float y, float *fr, float *fi, float *e)
     {
         f1t(a, 3.14159265358979f * y, fr, fi, e);
+    }
+    // exp(a) - 1 alone (the phase-free factor), the same series and range as f1t
+    static __device__ __forceinline__ float em1(float a)
+    {
+        if (a >= -0.5f) {
+            float p = 1.0f / 40320.0f;
+            p = fmaf(p, a, 1.0f / 5040.0f);
+            p = fmaf(p, a, 1.0f / 720.0f);
+            p = fmaf(p, a, 1.0f / 120.0f);
+            p = fmaf(p, a, 1.0f / 24.0f);
+            p = fmaf(p, a, 1.0f / 6.0f);
+            p = fmaf(p, a, 0.5f);
+            p = fmaf(p, a, 1.0f);
+            return a * p;
+        }
+        return em1_far(a);
     }
     // the same from the phase t = pi y (the hot loop forms t directly; beyond the series' range y is
     // recomputed from t)
@@ -531,7 +548,7 @@ template <typename T, int N, int V> struct Fused {
 #pragma unroll
             for (int m = 0; m < RM; ++m) {
                 C w{};
-                if (m) w = PADT ? tw_load(tw, m * k) : tw[m * k];
+                if (m) w = PADT ? tw_load(tw, m * k) : tw_at(tw, m * k);
 #pragma unroll
                 for (int q = 0; q < PER; ++q) {
                     cpx<T> v = buf[pad(g + q * G + m * NB)];
@@ -552,8 +569,20 @@ template <typename T, int N, int V> struct Fused {
         }
     }
 
-    // twiddle tables of the middle passes live in shared memory (tw1: W_{R M1}, tw2: W_{R M1 M2})
-    static __device__ __forceinline__ C tw_load(const C *tw, int t) { return tw[tw_index(t)]; }
+    // twiddle tables of the middle passes live in shared memory (tw1: W_{R M1}, tw2: W_{R M1 M2}).  The
+    // FP32 entry (hi+lo, 16 bytes) is read as one 16-byte load: read field by field (four 4-byte
+    // loads at a 16-byte stride), the loads of a warp met 2-way bank conflicts each -- 45% of all
+    // shared-memory conflicts of the step counted by ncu at N = 4096
+    static __device__ __forceinline__ C tw_at(const C *tw, int i)
+    {
+        if constexpr (sizeof(T) == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(tw + i);
+            return C{v.x, v.y, v.z, v.w};
+        } else {
+            return tw[i];
+        }
+    }
+    static __device__ __forceinline__ C tw_load(const C *tw, int t) { return tw_at(tw, tw_index(t)); }
 
     // S (E/odd layout in buf), optionally times K_T, at the first-pass indices -> DST -> E/odd layout
     static __device__ __forceinline__ void dst(cpx<T> *x, cpx<T> *buf, const Tables<T> &tb, int g, Carry<T> *wtot,
@@ -640,8 +669,21 @@ template <typename T, int N, int V> struct Pointwise {
     static __device__ typename NormSum<T>::type factor(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode,
                                                        T A, T B, T D, double *red)
     {
-        const SC *tab = (mode == 1) ? tb.statV2 : tb.statV;
         SqAcc<T> acc, acc_odd;   // even and odd j accumulate separately (two dependency chains)
+        // a medium with gamma_hat = 0 has no dynamic phase (B = 0 exactly): the FP32 form then skips
+        // the sine and cosine series, whose value would be exactly 0 -- the same arithmetic
+        if (sizeof(T) == 4 && B == (T)0) factor_pts<false>(buf, tb, g, c, l, mode, A, B, D, acc, acc_odd);
+        else factor_pts<true>(buf, tb, g, c, l, mode, A, B, D, acc, acc_odd);
+        if (mode == 0) return {};
+        acc.merge(acc_odd);
+        return slot_norm_sum<T, G>(acc, red);
+    }
+
+    template <bool phase>
+    static __device__ __forceinline__ void factor_pts(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode,
+                                                      T A, T B, T D, SqAcc<T> &acc, SqAcc<T> &acc_odd)
+    {
+        const SC *tab = (mode == 1) ? tb.statV2 : tb.statV;
         const T Bpi = (T)3.14159265358979323846 * B;   // the phase coefficient: t = pi B j^2
 #pragma unroll 2
         for (int k = g; k < N / 2; k += G) {
@@ -654,13 +696,18 @@ template <typename T, int N, int V> struct Pointwise {
                 // step; it is applied as w + w f1 with f1 its deviation from 1, evaluated so that the
                 // rounding is relative to f1, not to 1 (a rounding of a value next to 1 would repeat
                 // identically every step and add up)
-                T f1r, f1i, em1;
+                T f1r, f1i = (T)0, em1;
                 T z = (T)0;
                 if constexpr (sizeof(T) == 4) {
                     // j^2 is exact in FP32 up to N = 4096 (and rounded once above); the coefficients
                     // change every step, so no rounding of a, t or z repeats from step to step
                     const T j2 = fj * fj;
-                    Dyn<T>::f1t(A * j2, Bpi * j2, &f1r, &f1i, &em1);
+                    if (phase) {
+                        Dyn<T>::f1t(A * j2, Bpi * j2, &f1r, &f1i, &em1);
+                    } else {   // gamma_hat = 0: the phase is 0 and f1 = exp(a) - 1 exactly as f1t gives it
+                        em1 = Dyn<T>::em1(A * j2);
+                        f1r = em1;
+                    }
                     z = D * j2;
                 } else {
                     Dyn<T>::f1((A * fj) * fj, (B * fj) * fj, &f1r, &f1i, &em1);
@@ -677,14 +724,16 @@ template <typename T, int N, int V> struct Pointwise {
                     else ac.add_w(v, mag * ((T)1 + z * ((T)1 + z * ((T)0.5 + z * (T)(1.0 / 6.0)))));
                 }
                 const cpx<T> w = PR::mul_s(v, stat(tb, tab, c, l, j, mode == 1));
-                v = mk(w.x + (w.x * f1r - w.y * f1i), w.y + (w.x * f1i + w.y * f1r));
+                if constexpr (sizeof(T) == 4) {   // w + w f1, fused
+                    v = phase ? mk(fmaf(w.x, f1r, fmaf(-w.y, f1i, w.x)), fmaf(w.y, f1r, fmaf(w.x, f1i, w.y)))
+                              : mk(fmaf(w.x, f1r, w.x), fmaf(w.y, f1r, w.y));
+                } else {
+                    v = mk(w.x + (w.x * f1r - w.y * f1i), w.y + (w.x * f1i + w.y * f1r));
+                }
                 if (mode == 2) ac.add_w(v, (T)1);
                 buf[p] = v;
             }
         }
-        if (mode == 0) return {};
-        acc.merge(acc_odd);
-        return slot_norm_sum<T, G>(acc, red);
     }
 
     static __device__ cpx<double> to_d(const typename Prec<double>::C &a) { return a; }

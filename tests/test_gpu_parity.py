@@ -121,8 +121,10 @@ def check_fp32(q, obs, ref, u, uref, min_same=0.85):
     N = u.shape[1]
     dm = np.abs(obs["surv"].mean(axis=0) - ref["surv"].mean(axis=0))
     assert dm.max() <= FP32_ENSEMBLE_ABS, dm
+    lazy = lazy_shortcut(q, obs, ref)
     same = (obs["jump_digest"] == ref["jump_digest"]) & (obs["n_jumps"] == ref["n_jumps"]) & \
-           (obs["l"] == ref["l"]) & (obs["color"] == ref["color"])
+           (obs["l"] == ref["l"]) & (obs["color"] == ref["color"]) & \
+           ((obs["n_steps_exec"] == ref["n_steps_exec"]) | lazy)
     assert same.mean() >= min_same, same.mean()
     steps = np.maximum(obs["n_steps_exec"], ref["n_steps_exec"])
     bound = fp32_bound(N, steps)
@@ -244,20 +246,23 @@ def test_caps(q, opt, precision):
             # 32-trajectory batch can flip, so the ensemble of this small batch is no test; the checks
             # are the fraction of identical jump sequences and, on those, the records and the
             # end-of-step norms of the capped trajectories within the FP32 error model
-            same = (obs["jump_digest"] == ref["jump_digest"]) & (obs["n_jumps"] == ref["n_jumps"]) & \
-                   (obs["l"] == ref["l"]) & (obs["color"] == ref["color"])
-            assert same.mean() >= FP32_MIN_SAME_LONG, same.mean()
+            # the trigger that stops a capped trajectory is not a jump, so the digest does not see it:
+            # identical also means stopped at the same step
             lazy = lazy_shortcut(q, obs, ref)
+            same = (obs["jump_digest"] == ref["jump_digest"]) & (obs["n_jumps"] == ref["n_jumps"]) & \
+                   (obs["l"] == ref["l"]) & (obs["color"] == ref["color"]) & \
+                   ((obs["n_steps_exec"] == ref["n_steps_exec"]) | lazy)
+            assert same.mean() >= FP32_MIN_SAME_LONG, same.mean()
             fr = ref["flags"] & ~q.F_BORDERLINE
             fr[lazy] &= ~q.F_NOJUMP_SHORTCUT
             assert np.array_equal(obs["flags"][same] & ~q.F_BORDERLINE, fr[same])
-            assert np.array_equal(obs["n_steps_exec"][same & ~lazy], ref["n_steps_exec"][same & ~lazy])
+            steps = np.maximum(obs["n_steps_exec"], ref["n_steps_exec"])
             cap = same & ((ref["flags"] & (q.F_MAXJUMPS | q.F_LCAP)) != 0)
             assert cap.any()
             dn = np.abs(obs["norm2"][cap] / ref["norm2"][cap] - 1)
-            assert (dn <= fp32_bound(64, ref["n_steps_exec"][cap])).all(), dn.max()
+            assert (dn <= fp32_bound(64, steps[cap])).all(), dn.max()
             rel = np.abs(obs["surv"][same] - ref["surv"][same]).max(axis=1)
-            assert (rel <= fp32_bound(64, ref["n_steps_exec"][same]) * np.maximum(1, ref["surv"][same].max(1))).all()
+            assert (rel <= fp32_bound(64, steps[same]) * np.maximum(1, ref["surv"][same].max(1))).all()
 
 
 @pytest.mark.parametrize("form,precision", [(0, 0), (1, 0), (0, 1)])
