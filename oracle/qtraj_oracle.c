@@ -382,7 +382,29 @@ double oqt_expmEi(double x)
 double oqt_ksu_phi(double a)
 {
     if (a <= 0) return 0.0;
-    return 1.0 - ((1.0 + a) * oqt_expmEi(a) + (1.0 - a) * oqt_expE1(a)) / (2.0 * a);
+    if (a >= 2.0) return 1.0 - ((1.0 + a) * oqt_expmEi(a) + (1.0 - a) * oqt_expE1(a)) / (2.0 * a);
+    /* below 2 the closed form loses digits to cancellation (phi ~ a^2 ln a while each term is O(1));
+     * the same expression expanded instead: with f(a) = (1+a) e^-a = sum_n (-1)^n (1-n) a^n / n! and
+     * P(a) = sum_{n>=1} a^n / (n n!) (so that Ei = gamma + ln a + P(a), E1 = -gamma - ln a - P(-a)),
+     * phi(a) = -sum_{odd m>=3} [(gamma + ln a)(m-1)/m! + c_m] a^(m-1), c_m the a^m coefficient of f P
+     * (the odd orders of f P above the first give the terms; its a^1 term cancels the 1) */
+    enum { NT = 40 };
+    double fc[NT], pc[NT], fact = 1.0;
+    for (int n = 0; n < NT; n++) {
+        if (n > 0) fact *= n;
+        fc[n] = ((n & 1) ? -1.0 : 1.0) * (1.0 - n) / fact;
+        pc[n] = n == 0 ? 0.0 : 1.0 / (n * fact);
+    }
+    double L = OQT_EULER_GAMMA + log(a), sum = 0.0, mfact = 1.0, apow = a * a;
+    for (int m = 1; m < NT; m++) {
+        mfact *= m;
+        if (m < 3 || !(m & 1)) continue;
+        double cm = 0.0;
+        for (int n = 0; n <= m; n++) cm += fc[n] * pc[m - n];
+        sum += (L * (m - 1) / mfact + cm) * apow;   /* apow = a^(m-1) */
+        apow *= a * a;
+    }
+    return -sum;
 }
 
 /* the KSU potential at r (singlet, angular momentum l) and temperature T: V_R + i V_I + l(l+1)/(M r^2) */

@@ -669,3 +669,148 @@ def test_trajectory_average_matches_lindblad(oracle_lib):
             f = np.mean((obs["color"] == c) & (obs["l"] == l) & alive)
             p = pops[c, l]
             assert abs(f - p) < 3.5 * np.sqrt(max(p * (1 - p), 1e-6) / nt), (c, l, f, p)
+
+
+# ------------------------------------------------------------------------------------------------
+# the isotropic KSU potential (App. E, "Isotropic KSU potential")
+# ------------------------------------------------------------------------------------------------
+def test_ksu_special_functions_match_library(oracle_lib):
+    """The oracle's own e^x E1(x) (series / continued fraction) and e^-x Ei(x) (series / asymptotic
+    series) against scipy's exp1 and expi, across the switch points."""
+    special = pytest.importorskip("scipy.special")
+    o = oracle_lib
+    for x in (1e-4, 0.01, 0.3, 0.999, 1.001, 2.0, 7.0, 20.0, 59.9, 60.1, 90.0, 300.0):
+        assert abs(o.expE1(x) / (np.exp(x) * special.exp1(x)) - 1) < 1e-13, x
+        assert abs(o.expmEi(x) / (np.exp(-x) * special.expi(x)) - 1) < 1e-13, x
+
+
+def test_ksu_phi_is_the_printed_integral(oracle_lib):
+    """phi(rhat) = 2 int_0^inf dz z/(z^2+1)^2 [1 - sin(z rhat)/(z rhat)] as printed: the oracle's
+    closed form and small-argument series against the integral itself (2 int z/(z^2+1)^2 = 1, and the
+    sine part by mpmath's oscillatory quadrature at 30 digits), and its limits phi(0) = 0,
+    phi -> 1 - 2/rhat^2."""
+    mp = pytest.importorskip("mpmath")
+    o = oracle_lib
+    mp.mp.dps = 30
+    for a in (0.05, 0.3, 1.0, 1.9, 2.1, 3.0, 10.0, 30.0):   # both sides of the series/closed-form switch
+        am = mp.mpf(a)
+        sine = mp.quadosc(lambda z: mp.sin(am * z) / (1 + z * z) ** 2, [0, mp.inf], omega=am)
+        assert abs(o.ksu_phi(a) - float(1 - 2 * sine / am)) < 1e-15, a
+    assert o.ksu_phi(0.0) == 0.0
+    xs = np.linspace(1e-3, 50, 400)
+    ph = np.array([o.ksu_phi(x) for x in xs])
+    assert (np.diff(ph) > 0).all() and 0 < ph[0] < 1e-5
+    assert abs(o.ksu_phi(200.0) - (1 - 2 / 200.0 ** 2)) < 1e-7
+
+
+def test_ksu_running_coupling(oracle_lib):
+    """alpha_s(5 GeV) = 0.2034 as printed, and the one-loop renormalisation-group equation
+    d alpha_s / d ln mu^2 = -b0 alpha_s^2, b0 = (11 Nc - 2 N_F)/(12 pi) with N_F = 3, by finite
+    differences."""
+    o = oracle_lib
+    assert o.alpha_s_run(5.0) == pytest.approx(0.2034, abs=1e-15)
+    b0 = (33.0 - 6.0) / (12 * np.pi)
+    for mu in (1.5, 2.5, 4.0, 12.0):
+        h = 1e-4                                                 # a step in ln mu^2
+        d = (o.alpha_s_run(mu * np.exp(h / 4)) - o.alpha_s_run(mu * np.exp(-h / 4))) / h
+        assert abs(d / (-b0 * o.alpha_s_run(mu) ** 2) - 1) < 1e-7, mu
+    assert o.alpha_s_run(2.0) > o.alpha_s_run(3.0) > o.alpha_s_run(5.0)
+
+
+def test_ksu_potential_limits(oracle_lib):
+    """The KSU potential (App. E): as T -> 0 (m_D -> 0) the KMS form becomes the Cornell -a/r + sigma r;
+    its real part never exceeds V_vac(r_SB) = -a/r_SB + sigma r_SB and equals it where the KMS form
+    would; the imaginary part is -alpha_s(2 pi T) C_F T phi(m_D r): 0 at r -> 0, tending to
+    -alpha_s C_F T; at T = 0 the potential is the vacuum Cornell with string breaking."""
+    o = oracle_lib
+    g = o.Grid(N=256, L=20.0)
+    a, sig, rsb = 0.409, 0.21, 1.25 / 0.1973269804
+    vcap = -a / rsb + sig * rsb
+    g0 = o.Grid(N=256, L=20.0, ksu_fmd=1e-9)               # m_D -> 0 at a physical temperature
+    for r in (0.05, 0.5, 2.0, 5.0):
+        v = o.ksu_potential(g0, 0, 0.3, r)
+        assert abs(v.real - (-a / r + sig * r)) < 1e-7 and abs(v.imag) < 1e-12, r
+    for r in (0.05, 0.5, 2.0, 6.0, 8.0):
+        v = o.ksu_potential(g, 0, 0.0, r)
+        assert v.imag == 0 and abs(v.real - ((-a / r + sig * r) if r <= rsb else vcap)) < 1e-14
+    T = 0.3
+    mD = o.ksu_debye_mass(g, T)
+    rs = np.linspace(0.02, 40.0, 2000)
+    v = np.array([o.ksu_potential(g, 0, T, r) for r in rs])
+    assert (v.real <= vcap + 1e-15).all() and abs(v.real[-1] - 2 * sig / mD) < 1e-10   # screened: 2 sigma/m_D
+    gc = o.Grid(N=256, L=20.0, ksu_fmd=0.3)                  # weak screening: 2 sigma/m_D above the cap
+    vc = np.array([o.ksu_potential(gc, 0, T, r) for r in rs])
+    assert 2 * sig / o.ksu_debye_mass(gc, T) > vcap
+    assert (vc.real <= vcap + 1e-15).all() and vc.real[-1] == vcap and (vc.real == vcap).sum() > 100
+    assert (np.abs(np.diff(vc.real[rs > 1.0])) < 0.02).all()   # continuous across the cap (slope < 1 GeV^2)
+    assert (v.imag <= 0).all() and abs(v.imag[0]) < 1e-3
+    asym = -o.alpha_s_run(2 * np.pi * T) * (4.0 / 3.0) * T
+    x = mD * rs[-1]
+    assert abs(v.imag[-1] / asym - (1 - 2 / x ** 2 - 8 / x ** 4)) < 1e-6   # phi's asymptotic series
+    assert o.ksu_potential(g, 2, T, 1.0).real - o.ksu_potential(g, 0, T, 1.0).real == pytest.approx(6.0 / 4.65, rel=1e-12)
+    assert o.ksu_debye_mass(g, 0.0) == 0.0
+    g2 = o.Grid(N=256, L=20.0, ksu_fmd=1.5)
+    assert o.ksu_debye_mass(g2, T) == pytest.approx(1.5 * mD, rel=1e-14)
+
+
+def test_ksu_vacuum_spectrum_independent_discretisation(oracle_lib):
+    """The KSU vacuum basis: eigenstates of the grid Hamiltonian with the Cornell potential (string
+    breaking at r_SB).  Its 1S and 1P energies agree with a second discretisation of the same radial
+    problem (a three-point Laplacian on a 4x finer grid, scipy's tridiagonal eigensolver)."""
+    linalg = pytest.importorskip("scipy.linalg")
+    from oracle import eigen
+    o = oracle_lib
+    g = o.Grid(N=1024, L=16.0, potential=1)
+    for l in (0, 1):
+        w, _ = eigen.vacuum_eigenstates(g, l, 1)
+        Nf = 8192
+        dr = g.L / Nf
+        r = np.arange(1, Nf) * dr
+        V = eigen.vacuum_potential(g, r) + l * (l + 1) / (g.M * r * r)
+        d = V + 2.0 / (g.M * dr * dr)                          # -u''/M with the reduced mass M/2
+        e = np.full(len(r) - 1, -1.0 / (g.M * dr * dr))
+        wf = linalg.eigh_tridiagonal(d, e, select="i", select_range=(0, 0))[0][0]
+        assert abs(w[0] - wf) < 2e-4, (l, w[0], wf)
+
+
+def test_ksu_evolution_has_no_jumps_and_decays_by_v_i(oracle_lib):
+    """Evolution with the KSU potential (singlet, H_eff, no collapse operator): no jump and r0 = 0 in
+    any record; the norm falls at the rate -d|psi|^2/dt = -2 <psi|V_I|psi> (to O(dt^2)); the survival
+    ratio is the unnormalised |<1S|psi>|^2 / |<1S|psi_0>|^2; at a vanishing temperature the vacuum
+    1S stays put (S = 1, norm 1)."""
+    from oracle import eigen
+    o = oracle_lib
+    g = o.Grid(N=256, L=12.0, dt=0.001, potential=1)
+    g.basis = eigen.numerical_basis(g)
+    _, v1s = eigen.vacuum_eigenstates(g, 0, 1)
+    inits = [o.given_state(v1s[0], 1, 0, 0), o.init_spec("gauss", 0.5, 1, 0, 0)]
+    media = [o.medium(T0=0.45, tau0=0.6, Tf=0.35, kappa_hat=0.0)]
+    idx = np.array([0, 1, 0, 1], np.int32)
+    mi = np.zeros(4, np.int32)
+    ref, _, u = o.run_batch(g, inits, idx, media, mi, np.arange(4, dtype=np.uint64), want_states=True)
+    assert (ref["n_jumps"] == 0).all() and (ref["r0"] == 0).all() and (ref["n_steps_exec"] > 100).all()
+    assert (ref["norm2"] < 0.99).all() and np.array_equal(ref["surv"][0], ref["surv"][2])   # deterministic
+    ov2 = ref["ov_re"][:, 0] ** 2 + ref["ov_im"][:, 0] ** 2
+    o0 = (g.L / g.N) * np.dot(g.basis[0], v1s[0])
+    assert np.allclose(ref["surv"][0, 0], ov2[0] / o0 ** 2, rtol=1e-12)   # not divided by the norm
+    # with m_D -> 0 the potential is the vacuum one: the vacuum 1S keeps S = 1 and its norm
+    g0 = o.Grid(N=256, L=12.0, dt=0.001, potential=1, ksu_fmd=1e-12)
+    g0.basis = g.basis
+    r0_, _, _ = o.run_batch(g0, inits[:1], np.zeros(1, np.int32), media, np.zeros(1, np.int32), np.zeros(1, np.uint64))
+    assert abs(r0_["norm2"][0] - 1) < 1e-10 and abs(r0_["surv"][0, 0] - 1) < 1e-8
+    # decay rate at constant T
+    m = o.medium(T0=0.4, tau0=1e9, Tf=0.39, kappa_hat=0.0)
+    errs = []
+    for dt in (0.001, 0.0005):
+        h_ = o.Grid(N=256, L=12.0, dt=dt, potential=1)
+        dr = h_.L / h_.N
+        r = np.arange(h_.N) * dr
+        u0 = o.initial_state(h_, o.init_spec("gauss", 0.8, 1, 0, 0))
+        nst = int(round(0.1 / dt))
+        uu, hh = o.evolve_nojump(h_, u0, 0, 0, m, 0, nst)
+        _, h1 = o.evolve_nojump(h_, uu, 0, 0, m, nst, 1)
+        rate = -(h1[0] - hh[-2]) / (2 * dt)
+        VI = np.array([o.ksu_potential(h_, 0, 0.4, x).imag if x > 0 else 0.0 for x in r])
+        gam = -2.0 * dr * np.sum(VI * np.abs(uu) ** 2)
+        errs.append(abs(rate - gam) / gam)
+    assert errs[0] < 1e-5 and 3.0 < errs[0] / errs[1] < 5.0
