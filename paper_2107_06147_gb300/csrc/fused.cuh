@@ -38,11 +38,6 @@ namespace qt {
 
 // V selects the launch variant (fused_launch.cuh); variants 2 and 3 use radix 8 for N >= 1024:
 // twice the threads per trajectory, half the registers per thread, one more FFT pass.
-// shared-memory index of entry t of a middle-pass twiddle table: one pad entry every 8 (16-byte
-// entries), so that the stride-m reads tw[m k] of a warp spread over all bank groups (unpadded, an
-// even m put up to 16 lanes on one bank group)
-__host__ __device__ constexpr int tw_index(int t) { return t + (t >> 3); }
-__host__ __device__ constexpr int tw_entries(int n) { return n == 0 ? 0 : tw_index(n - 1) + 1; }
 
 template <int N, int V = 0> struct FusedPlan {
     static constexpr int R = (N <= 32) ? 4 : (N <= 512) ? 8 : (V == 2 || V == 3 ? 8 : 16);
@@ -52,12 +47,12 @@ template <int N, int V = 0> struct FusedPlan {
     static constexpr int M1 = MID >= 16 ? 16 : MID;
     static constexpr int M2 = MID / M1;          // 1, 2, 4, 8 or 16
     static constexpr int BUF = N + N / R + 8;    // padded FFT extent; also holds the E/odd layout
-    // The second middle-pass twiddle table is padded like the first only for M2 > 2: with M2 = 2 its
-    // reads tw[k] are consecutive across a warp.  At N = 8192 (FP32) the 1 KB saved lets two CTAs
-    // fit the 164 KB shared-memory carveout instead of 196 KB, i.e. 92 KB of L1 instead of 60 KB for
-    // the per-step tables (measured +3.2%).
-    static constexpr bool PAD2 = M2 > 2;
-    static constexpr int TW2 = M2 > 1 ? (PAD2 ? tw_entries(R * M1 * M2) : R * M1 * M2) : 0;
+    // middle-pass twiddle tables in shared memory, row m holding W^(m k) for the k of every thread
+    // (tw1: [M1][R] of W_{R M1}; tw2: [M2][R M1] of W_{R M1 M2}), so that a warp reads consecutive
+    // entries.  (A flat table W^t read at t = m k with one pad entry every 8 met up to 7-way bank
+    // conflicts at odd m -- 44% of the step's shared-memory conflicts at N = 4096.)
+    static constexpr int TW1 = R * M1;
+    static constexpr int TW2 = M2 > 1 ? R * M1 * M2 : 0;
     static_assert(N == R * M1 * M2 * R, "plan");
 };
 
@@ -109,17 +104,19 @@ template <> struct SqAcc<double> {
     __device__ __forceinline__ double value() const { return v; }
 };
 
-// compensated complex value for the scan's carries between threads.  Chunk totals use cascaded
-// summation (the TwoSum error terms are collected separately); carries between threads are
-// double-float additions.
+// compensated complex value for the scan's carries between threads.  A thread's chunk total (R
+// terms of the chunk it owns) is a plain FP32 sum -- its rounding is of the order of the chunk's own
+// FFT rounding; the carries between threads, which accumulate the whole prefix and reach every later
+// coefficient, are double-float additions.  (Compensated chunk totals too cost 5% of the step at
+// N = 4096 for no change of the ensemble means or of the jump-sequence agreement measured beyond the
+// noise of a 1024-trajectory paired study.)
 template <typename T> struct Carry;
 template <> struct Carry<float> {
     DF re{0.f, 0.f}, im{0.f, 0.f};
     __device__ __forceinline__ void add(cpx<float> a)
     {
-        const DF r = two_sum(re.hi, a.x), i = two_sum(im.hi, a.y);
-        re = DF{r.hi, re.lo + r.lo};
-        im = DF{i.hi, im.lo + i.lo};
+        re.hi += a.x;
+        im.hi += a.y;
     }
     __device__ __forceinline__ void add(const Carry &o) { re = df_add(re, o.re); im = df_add(im, o.im); }
     __device__ __forceinline__ cpx<float> plus(cpx<float> a) const   // this + a, one rounding of the sum
@@ -537,8 +534,8 @@ template <typename T, int N, int V> struct Fused {
     // One middle pass (radix RM after PP points): butterfly i reads [i + m N/RM], multiplies by
     // W_{PP RM}^{m k} (k = i mod PP) and writes [(i - k) RM + k + m PP].  A thread's butterflies are
     // g + q G; when PP <= G they share k = g mod PP and so their twiddles, which are loaded once per m
-    // (from tw, a table of W_{PP RM}^t, t < PP RM).
-    template <int RM, int PP, bool PADT = true>
+    // (from tw, the table [RM][PP] of W_{PP RM}^{m k}).
+    template <int RM, int PP>
     static __device__ __forceinline__ void mid_pass(cpx<T> *x, cpx<T> *buf, const C *tw, int g)
     {
         if constexpr (RM > 1) {
@@ -548,7 +545,7 @@ template <typename T, int N, int V> struct Fused {
 #pragma unroll
             for (int m = 0; m < RM; ++m) {
                 C w{};
-                if (m) w = PADT ? tw_load(tw, m * k) : tw_at(tw, m * k);
+                if (m) w = tw_at(tw, m * PP + k);
 #pragma unroll
                 for (int q = 0; q < PER; ++q) {
                     cpx<T> v = buf[pad(g + q * G + m * NB)];
@@ -569,10 +566,8 @@ template <typename T, int N, int V> struct Fused {
         }
     }
 
-    // twiddle tables of the middle passes live in shared memory (tw1: W_{R M1}, tw2: W_{R M1 M2}).  The
-    // FP32 entry (hi+lo, 16 bytes) is read as one 16-byte load: read field by field (four 4-byte
-    // loads at a 16-byte stride), the loads of a warp met 2-way bank conflicts each -- 45% of all
-    // shared-memory conflicts of the step counted by ncu at N = 4096
+    // twiddle tables of the middle passes live in shared memory (FusedPlan: TW1, TW2); an FP32 entry
+    // (hi+lo, 16 bytes) is one 16-byte load
     static __device__ __forceinline__ C tw_at(const C *tw, int i)
     {
         if constexpr (sizeof(T) == 4) {
@@ -582,7 +577,6 @@ template <typename T, int N, int V> struct Fused {
             return tw[i];
         }
     }
-    static __device__ __forceinline__ C tw_load(const C *tw, int t) { return tw_at(tw, tw_index(t)); }
 
     // S (E/odd layout in buf), optionally times K_T, at the first-pass indices -> DST -> E/odd layout
     static __device__ __forceinline__ void dst(cpx<T> *x, cpx<T> *buf, const Tables<T> &tb, int g, Carry<T> *wtot,
@@ -607,7 +601,7 @@ template <typename T, int N, int V> struct Fused {
         }
         __syncthreads();
         mid_pass<P::M1, R>(x, buf, tw1, g);
-        mid_pass<P::M2, R * P::M1, P::PAD2>(x, buf, tw2, g);
+        mid_pass<P::M2, R * P::M1>(x, buf, tw2, g);
         // last pass (radix R, stride N/R): inputs [b + m NR], twiddle W^(m b).  For the mirror butterfly
         // b2 = NR - g, W^(m b2) = W_R^m conj(W^(m g)): one table load serves both (g = 0 pairs
         // 0 with NR/2, whose twiddles are loaded directly).
@@ -967,16 +961,17 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
     using C = typename Prec<T>::C;
     using P = FusedPlan<N, V>;
     C *tw1 = reinterpret_cast<C *>(buf + P::BUF);
-    C *tw2 = tw1 + tw_entries(P::R * P::M1);
+    C *tw2 = tw1 + P::TW1;
     Carry<T> *wtot = reinterpret_cast<Carry<T> *>(tw2 + P::TW2);
     double *red = reinterpret_cast<double *>(wtot + (G / 32 + 1));
     __shared__ int s_traj;
-    // middle-pass twiddles W_{R M1}^t and W_{R M1 M2}^t (the second only with a second middle pass),
-    // copied once per CTA
-    for (int t = threadIdx.x; t < P::R * P::M1; t += G) tw1[tw_index(t)] = Prec<T>::ld(&tb.W[t * (N / (P::R * P::M1))]);
+    // middle-pass twiddles, row m of a table holding W^(m k) for every k (tw1: [M1][R] of W_{R M1},
+    // tw2: [M2][R M1] of W_{R M1 M2}, the second only with a second middle pass), built once per CTA
+    for (int t = threadIdx.x; t < P::TW1; t += G)
+        tw1[t] = Prec<T>::ld(&tb.W[(t / P::R) * (t % P::R) * (N / P::TW1)]);
     if (P::M2 > 1)
-        for (int t = threadIdx.x; t < P::R * P::M1 * P::M2; t += G)
-            tw2[P::PAD2 ? tw_index(t) : t] = Prec<T>::ld(&tb.W[t * (N / (P::R * P::M1 * P::M2))]);
+        for (int t = threadIdx.x; t < P::TW2; t += G)
+            tw2[t] = Prec<T>::ld(&tb.W[(t / P::TW1) * (t % P::TW1) * (N / P::TW2)]);
 
     const int g = threadIdx.x;
     const double dr = tb.dr;
@@ -1209,7 +1204,7 @@ template <typename T, int N, int V> constexpr int fused_smem_bytes()
 {
     using P = FusedPlan<N, V>;
     return P::BUF * (int)sizeof(cpx<T>) +
-           (tw_entries(P::R * P::M1) + P::TW2) *
+           (P::TW1 + P::TW2) *
                (int)sizeof(typename Prec<T>::C) +
            (P::G / 32 + 1) * (int)sizeof(Carry<T>) + (P::G / 32 + 1) * 8 + 16;
 }
