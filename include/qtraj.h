@@ -76,6 +76,19 @@ typedef struct {
                         eigenstates of the discretised singlet vacuum Hamiltonian of the grid (the
                         propagator's V and kinetic factor), computed at qtraj_create by a
                         preconditioned block eigensolver (the paper's ProjType 1); needs alpha_s > 0. */
+    int potential;   /* Table 1 "potential": 0 = the OQS+pNRQCD potential of App. E with quantum jumps;
+                        1 = the isotropic KSU potential (App. E, "Isotropic KSU potential"): singlet
+                        only, deterministic evolution with H_eff and no jumps (Sec. 2.6: there are no
+                        collapse operators for it).  Its real part is the Karsch-Mehr-Satz form with
+                        a = 0.409, sigma = 0.21 GeV^2, capped at the vacuum Cornell value at
+                        r_SB = 1.25 fm; its imaginary part is -alpha_s C_F T phi(m_D r); m_D =
+                        F_mD T sqrt(Nc (1 + N_F/6) pi C_F alpha_s(2 pi T)) with alpha_s(mu) at one
+                        loop from alpha_s(5 GeV) = 0.2034 and N_F = 3.  The overlap basis is the
+                        numerical eigenstates of the grid's vacuum Hamiltonian with the Cornell
+                        potential (basis is ignored), and the survival ratios are the unnormalised
+                        |<s|psi>|^2 / |<s|psi_0>|^2 (the norm lost to V_I is the dissociation).
+                        Fused form only, no vacuum evolution (t_vacuum = 0), media with Tf >= 0.1 GeV. */
+    double ksu_mD_factor; /* F_mD of the KSU Debye mass (> 0; 1 = the perturbative m_D) */
 } qtraj_params;
 
 /* Initial state (Table 1, initType/initWidth/initN/initL/initC): kind 0 is the Gaussian

@@ -109,6 +109,7 @@ struct qtraj_ctx {
     double *prof = nullptr; // profile store of tabulated media: (tau, T) pairs
     std::vector<double> prof_host;
     double r1s = 1.0;       // <1S|r|1S> on the grid
+    void *phi_tab = nullptr; // KSU: (phi, h phi') at the nodes of [KSU_PHI_A0, KSU_PHI_A1]
     std::vector<double> basis_host;   // [NBASIS][N] the overlap basis (analytic or numerical)
     qtraj_trace_rec *trace = nullptr;   // per-step summary (caller buffers), off when trace_every == 0
     int *trace_cnt = nullptr;
@@ -135,6 +136,54 @@ struct qtraj_ctx {
 };
 
 namespace {
+
+// ------------------------------------------------------------------------------------------------
+// The isotropic KSU potential (App. E): constants as printed, and phi(rhat) tabulated for the kernels
+// ------------------------------------------------------------------------------------------------
+constexpr double KSU_A = 0.409, KSU_SIGMA = 0.21, KSU_RSB = 1.25 / HBARC;   // GeV^-1
+constexpr double KSU_ALPHA0 = 0.2034, KSU_MU0 = 5.0;                        // alpha_s(5 GeV)
+constexpr int KSU_NF = 3;
+constexpr double KSU_TF_MIN = 0.1;   // GeV: the one-loop alpha_s(2 pi T) stays below ~0.5 above it
+constexpr double EULER_G = 0.57721566490153286061;
+
+// e^-x Ei(x) and e^x E1(x) for x >= 2 (power series of Ei -- positive terms -- up to 60 and its
+// asymptotic series above; continued fraction of E1)
+double ksu_eEi(double x)
+{
+    if (x <= 60.0) {
+        double term = 1.0, sum = 0.0;
+        for (int k = 1; k < 400; ++k) {
+            term *= x / k;
+            sum += term / k;
+            if (term / k < 1e-18 * sum) break;
+        }
+        return std::exp(-x) * (EULER_G + std::log(x) + sum);
+    }
+    double t = 1.0 / x, sum = 0.0;
+    for (int k = 0; k < 200 && t > 1e-18 * sum; ++k) {
+        sum += t;
+        t *= (k + 1.0) / x;
+    }
+    return sum;
+}
+double ksu_eE1(double x)
+{
+    // e^x E1(x) = 1/(x+1 - 1^2/(x+3 - 2^2/(x+5 - ...))), evaluated from the tail
+    double f = x + 201.0;
+    for (int i = 100; i >= 1; --i) f = x + 2.0 * i - 1.0 - (double)i * i / f;
+    return 1.0 / f;
+}
+
+// phi(a) = 1 - [(1+a) e^-a Ei(a) + (1-a) e^a E1(a)] / (2a) and its derivative (a >= 2), for the
+// table the kernels interpolate: d/da e^-a Ei(a) = 1/a - e^-a Ei(a), d/da e^a E1(a) = e^a E1(a) - 1/a
+void ksu_phi_d(double a, double *phi, double *dphi)
+{
+    const double F = ksu_eEi(a), G = ksu_eE1(a);
+    const double B = (1.0 + a) * F + (1.0 - a) * G;
+    const double dB = 2.0 - a * (F + G);
+    *phi = 1.0 - B / (2.0 * a);
+    *dphi = -dB / (2.0 * a) + B / (2.0 * a * a);
+}
 
 struct Layout {
     size_t trajs, obs, gtrajs, gobs, gready, ctr, states, plain, total;
@@ -212,7 +261,70 @@ template <typename T> qtraj_status build_tables(qtraj_ctx *c)
         KT[k] = Prec<T>::make(std::cos(ph) * 2.0 / N, std::sin(ph) * 2.0 / N);
     }
     const double Nc = c->p.Nc, CF = (Nc * Nc - 1.0) / (2.0 * Nc);
-    const double coul[2] = {-CF * c->p.alpha_s, c->p.alpha_s / (2.0 * Nc)};
+    double coul[2] = {-CF * c->p.alpha_s, c->p.alpha_s / (2.0 * Nc)};
+    if (c->p.potential == 1) {
+        // KSU: the static factor holds the Cornell -a/r (and the centrifugal term); the kernels apply
+        // the rest of the potential, V_R + a/r and V_I, each step.  Phi is tabulated on
+        // [KSU_PHI_A0, KSU_PHI_A1] as (phi, h phi') for cubic Hermite interpolation (error below
+        // h^4/384 max|phi''''| ~ 3e-12), followed by the coefficients of its small-argument series
+        // phi(a) = -sum_k [ln a (gamma_k) + c_k] a^(2k), from the expansion of the closed form in
+        // Ei and E1: gamma_k = (m-1)/m!, c_k the a^m coefficient of (1+a)e^-a sum_{n>=1} a^n/(n n!),
+        // m = 2k+1, plus gamma (m-1)/m! folded into c_k.
+        coul[0] = coul[1] = -KSU_A;
+        std::vector<T> tab(2 * (size_t)KSU_PHI_NODES + 2 * (size_t)KSU_PHI_SER);
+        const double h = 1.0 / KSU_PHI_PER;
+        for (int i = 0; i < KSU_PHI_NODES; ++i) {
+            double ph, dph;
+            const double a = KSU_PHI_A0 + i * h;
+            if (a >= 2.0) {
+                ksu_phi_d(a, &ph, &dph);
+            } else {   // below 2 the series, and its derivative, in long double
+                long double f[48], pc[48], fact = 1, sum = 0, dsum = 0;
+                for (int n = 0; n < 48; ++n) {
+                    if (n) fact *= n;
+                    f[n] = ((n & 1) ? -1.0L : 1.0L) * (1.0L - n) / fact;
+                    pc[n] = n ? 1.0L / (n * fact) : 0.0L;
+                }
+                const long double La = (long double)EULER_G + std::log((long double)a);
+                long double mf = 1;
+                for (int m = 1; m < 48; ++m) {
+                    mf *= m;
+                    if (m < 3 || !(m & 1)) continue;
+                    long double cm = 0;
+                    for (int n = 0; n <= m; ++n) cm += f[n] * pc[m - n];
+                    const long double q = (long double)(m - 1) / mf;
+                    const long double am = std::pow((long double)a, (long double)(m - 1));
+                    sum += (La * q + cm) * am;
+                    dsum += ((m - 1) * (La * q + cm) + q) * am / a;
+                }
+                ph = (double)-sum;
+                dph = (double)-dsum;
+            }
+            tab[2 * (size_t)i] = (T)ph;
+            tab[2 * (size_t)i + 1] = (T)(h * dph);
+        }
+        {
+            double fact = 1.0, mf = 1.0;
+            std::vector<double> f(40), pc(40);
+            for (int n = 0; n < 40; ++n) {
+                if (n) fact *= n;
+                f[n] = ((n & 1) ? -1.0 : 1.0) * (1.0 - n) / fact;
+                pc[n] = n ? 1.0 / (n * fact) : 0.0;
+            }
+            for (int m = 1, k = 0; m < 40 && k < KSU_PHI_SER; ++m) {
+                mf *= m;
+                if (m < 3 || !(m & 1)) continue;
+                double cm = 0.0;
+                for (int n = 0; n <= m; ++n) cm += f[n] * pc[m - n];
+                const double q = (m - 1) / mf;
+                tab[2 * (size_t)KSU_PHI_NODES + 2 * k] = (T)q;                    // times ln a
+                tab[2 * (size_t)KSU_PHI_NODES + 2 * k + 1] = (T)(cm + EULER_G * q);
+                ++k;
+            }
+        }
+        CK(cudaMalloc(&c->phi_tab, sizeof(T) * tab.size()));
+        CK(cudaMemcpy(c->phi_tab, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice));
+    }
     // last-pass twiddles of the fused kernel, W^(m g) for m < R, g < G = N/(2R), one compact section
     // [R][G] (N/2 entries) per radix R = 16, 8, 4 at offsets 0, N/2, N: a kernel reads the section of
     // its own radix, and the threads of a warp read consecutive entries
@@ -274,6 +386,7 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     t.p_os = 2.0 / (Nc * Nc - 2.0);
     t.coul[0] = -(Nc * Nc - 1.0) / (2.0 * Nc) * c->p.alpha_s;
     t.coul[1] = c->p.alpha_s / (2.0 * Nc);
+    if (c->p.potential == 1) t.coul[0] = t.coul[1] = -KSU_A;   // the Cornell -a/r (static factor)
     t.max_jumps = c->p.max_jumps;
     t.l_cap = c->p.l_cap;
     t.use_rmin = c->p.use_rmin;
@@ -281,6 +394,22 @@ template <typename T> Tables<T> tables(const qtraj_ctx *c)
     t.ic_cplx = c->ic_cplx ? 1 : 0;
     t.prof = c->prof;
     t.r1s = c->r1s;
+    t.potential = c->p.potential;
+    t.phi_tab = (const T *)c->phi_tab;
+    t.phi_ser = (const T *)c->phi_tab + 2 * (size_t)KSU_PHI_NODES;
+    t.ksu_a_dr = (T)(KSU_A / c->dr);
+    t.ksu_sig_dr = (T)(KSU_SIGMA * c->dr);
+    t.ksu_two_sigma = (T)(2.0 * KSU_SIGMA);
+    t.ksu_cap = (T)(-KSU_A / KSU_RSB + KSU_SIGMA * KSU_RSB);
+    t.ksu_alpha0 = (T)KSU_ALPHA0;
+    t.ksu_b0 = (T)((11.0 * c->p.Nc - 2.0 * KSU_NF) / (12.0 * PI));
+    t.ksu_mu0sq = (T)(KSU_MU0 * KSU_MU0);
+    {
+        const double CF = (c->p.Nc * c->p.Nc - 1.0) / (2.0 * c->p.Nc);
+        t.ksu_md2 = (T)(c->p.ksu_mD_factor * c->p.ksu_mD_factor * c->p.Nc * (1.0 + KSU_NF / 6.0) * PI * CF);
+        t.ksu_cf = (T)CF;
+    }
+    t.ksu_dt = (T)c->dt;
     return t;
 }
 
@@ -396,6 +525,12 @@ qtraj_status numerical_states(const qtraj_ctx *c, int l, int m, std::vector<std:
 {
     const double Nc = c->p.Nc;
     EigenProblem ep{c->N, c->L, c->M, -(Nc * Nc - 1.0) / (2.0 * Nc) * c->p.alpha_s, c->p.deriv_type};
+    if (c->p.potential == 1) {
+        ep.potential = 1;
+        ep.a = KSU_A;
+        ep.sigma = KSU_SIGMA;
+        ep.r_sb = KSU_RSB;
+    }
     std::vector<std::vector<double>> start(m);
     for (int k = 0; k < m; ++k) coulomb_u(c->N, c->dr, c->a0, l + 1 + k, l, start[k]);
     std::vector<double> lam;
@@ -503,7 +638,14 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     if (p.t_vacuum > 0 && p.precision == QTRAJ_FP64 && N > 8192)
         return fail(QTRAJ_EINVAL, "the vacuum evolution runs in the fused form: FP64 needs N <= 8192");
     if (p.basis != 0 && p.basis != 1) return fail(QTRAJ_EINVAL, "basis must be 0 (analytic) or 1 (numerical)");
-    if (p.basis == 1 && !(p.alpha_s > 0)) return fail(QTRAJ_EINVAL, "the numerical basis needs alpha_s > 0");
+    if (p.potential != 0 && p.potential != 1) return fail(QTRAJ_EINVAL, "potential must be 0 (OQS+pNRQCD) or 1 (KSU)");
+    if (p.potential == 1) {
+        if (!(p.ksu_mD_factor > 0) || !std::isfinite(p.ksu_mD_factor)) return fail(QTRAJ_EINVAL, "ksu_mD_factor must be > 0");
+        if (p.form != QTRAJ_FUSED) return fail(QTRAJ_EINVAL, "the KSU potential runs in the fused form only");
+        if (p.t_vacuum > 0) return fail(QTRAJ_EINVAL, "the KSU potential has no vacuum evolution (t_vacuum = 0)");
+    } else if (p.basis == 1 && !(p.alpha_s > 0)) {
+        return fail(QTRAJ_EINVAL, "the numerical basis needs alpha_s > 0");
+    }
 
     qtraj_ctx *c = new qtraj_ctx();
     c->N = N;
@@ -513,6 +655,10 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     c->dr = L / N;
     c->p = p;
     c->a0 = 2.0 / (M * (p.Nc * p.Nc - 1.0) / (2.0 * p.Nc) * p.alpha_s);
+    if (p.potential == 1) {
+        c->p.basis = 1;                   // the Cornell vacuum eigenstates
+        c->a0 = 2.0 / (M * KSU_A);       // Coulomb-like start vectors of the eigensolver
+    }
     qtraj_status st = QTRAJ_OK;
     auto bail = [&](qtraj_status s) {
         qtraj_destroy(c);
@@ -520,7 +666,7 @@ qtraj_status qtraj_create(int N, double L, double dt, double M, const qtraj_para
     };
     // the overlap basis: analytic Coulomb states, or the numerical eigenstates of the grid's H
     c->basis_host.assign((size_t)NBASIS * N, 0.0);
-    if (p.basis == 1) {
+    if (c->p.basis == 1) {
         const int lm[3][2] = {{0, 3}, {1, 2}, {2, 1}};
         for (const auto &q : lm) {
             std::vector<std::vector<double>> v;
@@ -569,6 +715,7 @@ void qtraj_destroy(qtraj_ctx *c)
     free_ptr(c->sinpre);
     free_ptr(c->statV);
     free_ptr(c->statV2);
+    free_ptr(c->phi_tab);
     free_typed(c->eig);
     free_typed(c->ic);
     free_typed(c->ov0);
@@ -610,6 +757,7 @@ qtraj_status qtraj_init(qtraj_ctx *c, void *d_ws, size_t bytes, int n_traj, cons
         if (q.l < 0 || (q.color != 0 && q.color != 1)) return fail(QTRAJ_EINVAL, "spec %d: l >= 0, color 0/1", s);
         if (q.kind == 0 && !(q.width > 0)) return fail(QTRAJ_EINVAL, "spec %d: width must be positive", s);
         if (q.kind >= 1 && (q.n < 1 || q.l >= q.n)) return fail(QTRAJ_EINVAL, "spec %d: need 0 <= l < n", s);
+        if (c->p.potential == 1 && q.color != 0) return fail(QTRAJ_EINVAL, "spec %d: the KSU potential is singlet only", s);
     }
     std::vector<int> idx(n_traj);
     for (int t = 0; t < n_traj; ++t) {
@@ -716,6 +864,7 @@ qtraj_status qtraj_set_trace(qtraj_ctx *c, int every, int n_traced, int max_reco
     if (every < 0) return fail(QTRAJ_EINVAL, "every must be >= 0");
     if (every > 0) {
         if (c->p.form != QTRAJ_FUSED) return fail(QTRAJ_EINVAL, "the per-step summary needs the fused form");
+        if (c->p.potential != 0) return fail(QTRAJ_EINVAL, "the per-step summary is for the OQS+pNRQCD potential");
         if (n_traced <= 0 || max_records <= 0 || !d_records || !d_counts)
             return fail(QTRAJ_EINVAL, "n_traced, max_records and the buffers are required");
     }
@@ -767,6 +916,8 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
         if (const char *why = medium_check(q, c->prof_host.empty() ? nullptr : c->prof_host.data(),
                                            (int)(c->prof_host.size() / 2)))
             return fail(QTRAJ_EINVAL, "medium %d: %s", m, why);
+        if (c->p.potential == 1 && !(q.Tf >= KSU_TF_MIN))
+            return fail(QTRAJ_EINVAL, "medium %d: the KSU potential needs Tf >= %g GeV", m, KSU_TF_MIN);
         steps[m] = medium_steps(c->dt, q, c->prof_host.data());
         md[m] = encode_medium(c, q);
     }
@@ -793,7 +944,8 @@ qtraj_status qtraj_evolve(qtraj_ctx *c, int batch, const qtraj_medium *media, in
         tr[t] = TrajDev{(unsigned long long)seeds[t], sp, mi, steps[mi], g};
         if (steps[mi] > max_steps) max_steps = steps[mi];
     }
-    const int n_groups = c->p.use_rmin ? (int)gt.size() : 0;
+    // the rMin shortcut belongs to the jump algorithm; the KSU evolution has no jumps
+    const int n_groups = c->p.use_rmin && c->p.potential == 0 ? (int)gt.size() : 0;
 
     // staging: media | trajs | group trajs
     const size_t b_md = sizeof(MediumDev) * n_media, b_tr = sizeof(TrajDev) * batch, b_gt = sizeof(TrajDev) * gt.size();
@@ -1189,6 +1341,8 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
     for (int m = 0; m < n_media; ++m) {
         const qtraj_medium &q = media[m];
         if (const char *why = medium_check(q)) return fail(QTRAJ_EINVAL, "medium %d: %s", m, why);
+        if (c->p.potential == 1 && !(q.Tf >= KSU_TF_MIN))
+            return fail(QTRAJ_EINVAL, "medium %d: the KSU potential needs Tf >= %g GeV", m, KSU_TF_MIN);
         steps[m] = medium_steps(c->dt, q, nullptr);
         h.media[m] = encode_medium(c, q);
     }
@@ -1207,7 +1361,7 @@ extern "C" qtraj_status qtraj_evolve_static(qtraj_ctx *c, int batch, const qtraj
         }
         h.trajs[t] = TrajDev{(unsigned long long)seeds[t], sp, mi, steps[mi], gidx};
     }
-    if (!c->p.use_rmin) n_groups = 0;
+    if (!c->p.use_rmin || c->p.potential != 0) n_groups = 0;
 
     cudaStream_t s = (cudaStream_t)stream;
     auto up = [&](void *dst, const void *src, size_t n) -> cudaError_t {

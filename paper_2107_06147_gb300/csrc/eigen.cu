@@ -167,7 +167,9 @@ int vacuum_eigenstates(const EigenProblem &ep, int l, int m, const std::vector<s
     double vmax = 0.0, kmax = 0.0;
     for (int j = 1; j < N; ++j) {
         const double r = j * dr;
-        P.V[j] = ep.coul / r + l * (l + 1.0) / (ep.M * r * r);
+        const double vac = ep.potential == 1 ? (r <= ep.r_sb ? -ep.a / r + ep.sigma * r : -ep.a / ep.r_sb + ep.sigma * ep.r_sb)
+                                             : ep.coul / r;
+        P.V[j] = vac + l * (l + 1.0) / (ep.M * r * r);
         vmax = std::max(vmax, std::fabs(P.V[j]));
     }
     for (int k = 0; k < N; ++k) {
@@ -227,10 +229,20 @@ int vacuum_eigenstates(const EigenProblem &ep, int l, int m, const std::vector<s
         X.swap(Xn);
     }
     if (res_max >= 1e-13 * P.hnorm) return -2;
-    // discrete normalisation (L/N) sum u^2 = 1, sign: positive overlap with the start vector
+    // discrete normalisation (L/N) sum u^2 = 1, sign: positive overlap with the start vector (KSU:
+    // positive at the first point above 1e-3 of the largest value)
     out.assign(m, Vec(N, 0.0));
     for (int i = 0; i < m; ++i) {
-        const double s = dot(X[i], start[i]) < 0 ? -1.0 : 1.0;
+        double s = dot(X[i], start[i]) < 0 ? -1.0 : 1.0;
+        if (ep.potential == 1) {
+            double mx = 0.0;
+            for (int j = 0; j < N; ++j) mx = std::max(mx, std::fabs(X[i][j]));
+            for (int j = 0; j < N; ++j)
+                if (std::fabs(X[i][j]) > 1e-3 * mx) {
+                    s = X[i][j] < 0 ? -1.0 : 1.0;
+                    break;
+                }
+        }
         for (int j = 0; j < N; ++j) out[i][j] = s * X[i][j] / std::sqrt(dr);
     }
     return it;

@@ -9,6 +9,11 @@ struct EigenProblem {
     double L, M;     // box (GeV^-1), heavy-quark mass (GeV)
     double coul;     // coefficient of 1/r (the singlet's -C_F alpha_s)
     int deriv_type;  // kinetic factor as in the propagator: 0 p^2/M, 1 2[1 - cos(p dr)]/(M dr^2)
+    // vacuum potential of the isotropic KSU model instead of coul / r (potential 1): the Cornell
+    // -a/r + sigma r, constant beyond r_sb; its states are signed positive at their first point
+    // above 1e-3 of their largest value (the others: positive overlap with the start vector)
+    int potential = 0;
+    double a = 0, sigma = 0, r_sb = 0;
 };
 
 // The m lowest eigenvectors of H = V_l + K for angular momentum l, started from `start` (m vectors of

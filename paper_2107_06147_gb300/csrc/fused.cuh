@@ -104,19 +104,20 @@ template <> struct SqAcc<double> {
     __device__ __forceinline__ double value() const { return v; }
 };
 
-// compensated complex value for the scan's carries between threads.  A thread's chunk total (R
-// terms of the chunk it owns) is a plain FP32 sum -- its rounding is of the order of the chunk's own
-// FFT rounding; the carries between threads, which accumulate the whole prefix and reach every later
-// coefficient, are double-float additions.  (Compensated chunk totals too cost 5% of the step at
-// N = 4096 for no change of the ensemble means or of the jump-sequence agreement measured beyond the
-// noise of a 1024-trajectory paired study.)
+// compensated complex value for the scan's carries between threads.  Chunk totals use cascaded
+// summation (the TwoSum error terms are collected separately); carries between threads are
+// double-float additions.  The rounding of a chunk total is added to every later odd coefficient
+// (a step in k, energy growing with the number of coefficients after it): with plain FP32 chunk
+// totals the no-jump FP32 norm drifted by +7e-9 per step at N = 1024 (against < 5e-9 compensated),
+// so the 3% they would save at N = 4096 is not taken.
 template <typename T> struct Carry;
 template <> struct Carry<float> {
     DF re{0.f, 0.f}, im{0.f, 0.f};
     __device__ __forceinline__ void add(cpx<float> a)
     {
-        re.hi += a.x;
-        im.hi += a.y;
+        const DF r = two_sum(re.hi, a.x), i = two_sum(im.hi, a.y);
+        re = DF{r.hi, re.lo + r.lo};
+        im = DF{i.hi, im.lo + i.lo};
     }
     __device__ __forceinline__ void add(const Carry &o) { re = df_add(re, o.re); im = df_add(im, o.im); }
     __device__ __forceinline__ cpx<float> plus(cpx<float> a) const   // this + a, one rounding of the sum
@@ -379,6 +380,92 @@ __device__ __noinline__ typename Prec<T>::S static_far(double coul, double M, do
     double s, c;
     sincos(-V * dt * 0.5 * span, &s, &c);
     return Prec<T>::make_s(c, s);
+}
+
+// ------------------------------------------------------------------------------------------------
+// the isotropic KSU potential (App. E): per-step scalars at one temperature and the per-point
+// dynamic part V_R + a/r (the Cornell -a/r sits in the static factor) and V_I
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct KsuT {
+    T m;      // Debye mass m_D(T)
+    T two_s;  // 2 sigma / m_D
+    T gI;     // alpha_s(2 pi T) C_F T: V_I = -gI phi(m_D r)
+};
+
+__device__ __forceinline__ float k_log(float x) { return logf(x); }
+__device__ __forceinline__ double k_log(double x) { return log(x); }
+__device__ __forceinline__ float k_cbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double k_cbrt(double x) { return cbrt(x); }
+
+template <typename T> __device__ __forceinline__ KsuT<T> ksu_at(const Tables<T> &tb, T T3)
+{
+    const T Tt = k_cbrt(T3);
+    const T mu = (T)6.28318530717958647692 * Tt;
+    const T as = tb.ksu_alpha0 / ((T)1 + tb.ksu_alpha0 * tb.ksu_b0 * k_log(mu * mu / tb.ksu_mu0sq));
+    const T m = Tt * sqrt(tb.ksu_md2 * as);
+    return {m, tb.ksu_two_sigma / m, as * tb.ksu_cf * Tt};
+}
+
+// phi(x) of V_I: the small-argument series below KSU_PHI_A0, cubic Hermite interpolation of the
+// table up to KSU_PHI_A1, the asymptotic series 1 - sum_j (2j)! (2j+2) / x^(2j+2) above
+template <typename T> __device__ __forceinline__ T ksu_phi(const Tables<T> &tb, T x)
+{
+    if (x < (T)KSU_PHI_A0) {
+        const T y = x * x;
+        T pl = (T)0, pc = (T)0;
+#pragma unroll
+        for (int k = KSU_PHI_SER - 1; k >= 0; --k) {
+            pl = (pl + tb.phi_ser[2 * k]) * y;
+            pc = (pc + tb.phi_ser[2 * k + 1]) * y;
+        }
+        return x > (T)0 ? -(pl * k_log(x) + pc) : (T)0;
+    }
+    if (x < (T)KSU_PHI_A1) {
+        const T u = (x - (T)KSU_PHI_A0) * (T)KSU_PHI_PER;
+        int i = (int)u;
+        if (i > KSU_PHI_NODES - 2) i = KSU_PHI_NODES - 2;
+        const T s = u - (T)i, s2 = s * s, s3 = s2 * s;
+        const T *n = tb.phi_tab + 2 * i;
+        const T h00 = (T)2 * s3 - (T)3 * s2 + (T)1, h10 = s3 - (T)2 * s2 + s, h01 = (T)3 * s2 - (T)2 * s3, h11 = s3 - s2;
+        return h00 * n[0] + h10 * n[1] + h01 * n[2] + h11 * n[3];
+    }
+    const T q = (T)1 / (x * x);
+    T p = (T)6706022400.0;
+    p = fma(p, q, (T)43545600.0);
+    p = fma(p, q, (T)403200.0);
+    p = fma(p, q, (T)5760.0);
+    p = fma(p, q, (T)144.0);
+    p = fma(p, q, (T)8.0);
+    p = fma(p, q, (T)2.0);
+    return (T)1 - p * q;
+}
+
+// at grid point j > 0 and one temperature: vd = V_R + a/r (V_R = min(KMS, V_vac(r_SB))) and vi = V_I
+template <typename T> __device__ __forceinline__ void ksu_point(const Tables<T> &tb, const KsuT<T> &k, T fj, T &vd, T &vi)
+{
+    const T aor = tb.ksu_a_dr / fj, r_sig = tb.ksu_sig_dr * fj;     // a/r, sigma r
+    const T x = k.m * (fj * (T)tb.dr);
+    const T e = exp(-x);
+    // 1 - (1 + x) e^-x, by its series below 0.05 (the difference cancels there)
+    T g;
+    if (x < (T)0.05) {
+        T p = (T)(-1.0 / 3991680.0);              // the terms (-1)^n (n-1) x^n / n!, n = 2 .. 11
+        p = fma(p, x, (T)(1.0 / 403200.0));
+        p = fma(p, x, (T)(-1.0 / 45360.0));
+        p = fma(p, x, (T)(1.0 / 5760.0));
+        p = fma(p, x, (T)(-1.0 / 840.0));
+        p = fma(p, x, (T)(1.0 / 144.0));
+        p = fma(p, x, (T)(-1.0 / 30.0));
+        p = fma(p, x, (T)(1.0 / 8.0));
+        p = fma(p, x, (T)(-1.0 / 3.0));
+        p = fma(p, x, (T)0.5);
+        g = p * x * x;
+    } else {
+        g = (T)1 - ((T)1 + x) * e;
+    }
+    vd = aor * g + k.two_s * ((T)1 - e) - r_sig * e;   // KMS + a/r
+    if (vd - aor > tb.ksu_cap) vd = tb.ksu_cap + aor;  // the string-breaking cap
+    vi = -k.gI * ksu_phi(tb, x);
 }
 
 // in-place DFT of RR values (natural order in); output k lands in slot operm(k)
@@ -673,6 +760,49 @@ template <typename T, int N, int V> struct Pointwise {
         return slot_norm_sum<T, G>(acc, red);
     }
 
+    // The KSU counterpart of factor (same modes, same w + w f1 form): the dynamic exponent of the
+    // half-step at temperature T is (V_I - i (V_R + a/r)) dt/2 at each point, evaluated per point;
+    // ka, kb are the per-step scalars of T_n (the closing half-step) and T_{n+1} (the opening one).
+    static __device__ typename NormSum<T>::type factor_ksu(cpx<T> *buf, const Tables<T> &tb, int g, int l, int mode,
+                                                           const KsuT<T> &ka, const KsuT<T> &kb, double *red)
+    {
+        SqAcc<T> acc, acc_odd;
+        const SC *tab = (mode == 1) ? tb.statV2 : tb.statV;
+        const T hdt = (T)0.5 * tb.ksu_dt;
+#pragma unroll 1
+        for (int k = g; k < N / 2; k += G) {
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                const int j = 2 * k + par;
+                const int p = par ? K::odd_pos(k) : K::even_pos(k);
+                const T fj = (T)j;
+                T A = (T)0, t = (T)0, z = (T)0;
+                if (j > 0) {
+                    T vda = (T)0, via = (T)0, vdb = (T)0, vib = (T)0;
+                    if (mode != 0) ksu_point<T>(tb, ka, fj, vda, via);
+                    if (mode != 2) ksu_point<T>(tb, kb, fj, vdb, vib);
+                    A = (via + vib) * hdt;
+                    t = -(vda + vdb) * hdt;
+                    z = (via - vib) * hdt;   // |K_V(n)|^2 = exp(A + z)
+                }
+                T f1r, f1i, em1;
+                if constexpr (sizeof(T) == 4) Dyn<T>::f1t(A, t, &f1r, &f1i, &em1);
+                else Dyn<T>::f1(A, t * (T)0.318309886183790671537767526745, &f1r, &f1i, &em1);
+                const T mag = (T)1 + em1;
+                cpx<T> v = buf[p];
+                SqAcc<T> &ac = par ? acc_odd : acc;
+                if (mode == 1) ac.add_w(v, mag * exp(z));
+                const cpx<T> w = PR::mul_s(v, stat(tb, tab, 0, l, j, mode == 1));
+                v = mk(w.x + (w.x * f1r - w.y * f1i), w.y + (w.x * f1i + w.y * f1r));
+                if (mode == 2) ac.add_w(v, (T)1);
+                buf[p] = v;
+            }
+        }
+        if (mode == 0) return {};
+        acc.merge(acc_odd);
+        return slot_norm_sum<T, G>(acc, red);
+    }
+
     template <bool phase>
     static __device__ __forceinline__ void factor_pts(cpx<T> *buf, const Tables<T> &tb, int g, int c, int l, int mode,
                                                       T A, T B, T D, SqAcc<T> &acc, SqAcc<T> &acc_odd)
@@ -918,7 +1048,7 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
             }
         }
         // r0 > r_max is resolved only once r0 < p_NoJump is excluded; otherwise the kernel evolves it
-        if (dr0.r > tb.r_max && (have || !tb.use_rmin)) {
+        if (tb.potential == 0 && dr0.r > tb.r_max && (have || !tb.use_rmin)) {
             qtraj_obs o;
             for (int s = 0; s < NBASIS; ++s) { o.surv[s] = 0; o.ov_re[s] = 0; o.ov_im[s] = 0; }
             o.norm2 = 1.0;
@@ -945,7 +1075,7 @@ __device__ int fetch_trajectory(const Tables<T> &tb, const LaunchArgs &a)
 // for 768 and 1024.  FP64 holds twice the state and takes what the compiler needs.
 template <typename T, int N, int V> struct FusedBounds {
     static constexpr int G = FusedPlan<N, V>::G;
-    static constexpr int THREADS = (V == 0 || V == 4) ? 512 : V == 1 ? 640 : V == 2 ? 768 : 1024;
+    static constexpr int THREADS = (V == 0 || V == 4 || V == 5) ? 512 : V == 1 ? 640 : V == 2 ? 768 : 1024;
     static constexpr int MB = THREADS / G > 32 ? 32 : (THREADS / G > 0 ? THREADS / G : 1);
     static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? MB : 1;
 };
@@ -985,7 +1115,8 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         if (wk < 0) break;
         const bool grp = wk < a.n_groups;     // a group's no-jump run of this launch
         const int t = grp ? wk : wk - a.n_groups;
-        const bool nojump = a.nojump || grp;
+        constexpr bool KSU = V == 5;           // the isotropic KSU potential: H_eff only, no jumps
+        const bool nojump = a.nojump || grp || KSU;
 
         const TrajDev d = grp ? a.gtrajs[t] : a.trajs[t];
         const MediumDev md = tb.media[d.medium];
@@ -1005,7 +1136,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         }
         uint32_t kdraw = 0;
         Draws dw = draws(d.seed, 0u);
-        const double r0 = nojump ? 0.0 : dw.r;
+        const double r0 = nojump ? 0.0 : dw.r;   // (no draw is used without jumps)
         Threshold<T> thr;
         thr.set(nojump ? -1.0 : dw.r, dr);
         int nj = 0, flags = 0, fj = -1, lj = -1, ended = 0, executed = 0;
@@ -1014,7 +1145,7 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         // resolves r0 < p_NoJump by the shortcut first and r0 > r_max only otherwise.  The trajectory
         // is evolved: if its norm never falls to r0 it is the no-jump run (= the shortcut's record); the
         // first trigger shows r0 >= p_NoJump (the norm only decreases), and it ends as r_max does.
-        const bool rmax_pending = !nojump && dw.r > tb.r_max;
+        const bool rmax_pending = !nojump && !KSU && dw.r > tb.r_max;
         bool rmax_hit = false;
         const bool traced = V == 4 && !grp && a.trace_every > 0 && t < a.trace_n;
         int nrec = 0;
@@ -1031,9 +1162,12 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
         };
         T T3b = T3_of(0);
         T K3b = kappa_T3<T>(md.kfit, T3b);   // kappa_hat(T) T^3 when kappa_hat follows a lattice fit
+        KsuT<T> kb{};
+        if constexpr (KSU) kb = ksu_at<T>(tb, T3b);
         if (ns > 0) {
             __syncthreads();
-            PW::factor(buf, tb, g, c, l, 0, (T)md.erj[c] * K3b, (T)md.eij[c] * T3b, (T)0, red);
+            if constexpr (KSU) PW::factor_ksu(buf, tb, g, l, 0, kb, kb, red);
+            else PW::factor(buf, tb, g, c, l, 0, (T)md.erj[c] * K3b, (T)md.eij[c] * T3b, (T)0, red);
         }
 
         for (int n = 0; n < ns; ++n) {
@@ -1055,8 +1189,15 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                 }
             }
             const T Tsum = last ? T3a : T3a + T3b, Ksum = last ? K3a : K3a + K3b;
-            const auto n2s = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Ksum, eij * Tsum,
-                                        last ? (T)0 : erj * (K3a - K3b), red);   // norm^2 / dr
+            typename NormSum<T>::type n2s;   // norm^2 / dr
+            if constexpr (KSU) {
+                const KsuT<T> ka = kb;
+                kb = ksu_at<T>(tb, T3b);
+                n2s = PW::factor_ksu(buf, tb, g, l, last ? 2 : 1, ka, kb, red);
+            } else {
+                n2s = PW::factor(buf, tb, g, c, l, last ? 2 : 1, erj * Ksum, eij * Tsum,
+                                 last ? (T)0 : erj * (K3a - K3b), red);
+            }
             if (!thr.finite(n2s)) {
                 flags |= QTRAJ_F_NONFINITE;
                 ended = 1;
@@ -1160,7 +1301,9 @@ __global__ void __launch_bounds__(FusedPlan<N, V>::G, (FusedBounds<T, N, V>::MIN
                 o.ov_im[s] = ovi[s];
                 double sv = 0.0;
                 if (!ended && c == 0 && basis_l[s] == l) {
-                    const double prob = (ovr[s] * ovr[s] + ovi[s] * ovi[s]) / n2;
+                    // with jumps the estimator takes the normalised state; without (KSU) the norm lost
+                    // to V_I is the dissociation, and the overlap is taken unnormalised
+                    const double prob = (ovr[s] * ovr[s] + ovi[s] * ovi[s]) / (KSU ? 1.0 : n2);
                     if (tb.ov0_zero[sp * NBASIS + s]) sv = prob;
                     else {
                         const double a0 = tb.ov0[(sp * NBASIS + s) * 2], b0 = tb.ov0[(sp * NBASIS + s) * 2 + 1];

@@ -9,14 +9,16 @@ cudaError_t fused_launch_f32_c(int N, const Tables<float> &tb, const LaunchArgs 
 cudaError_t fused_launch_f32_b(int N, const Tables<float> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
                              cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
-    if (a.trace_every > 0) variant = 0;   // the per-step summary runs the traced twin of variant 0
+    // the per-step summary runs the traced twin of variant 0, the KSU potential its own twin of it
+    if (a.trace_every > 0 || tb.potential == 1) variant = 0;
     switch (N) {
     case 2048:
         switch (variant) {
         case 1: return fused_go<float, 2048, 1>(tb, a, sm_count, max_ctas, s, info, query_only);
         case 2: return fused_go<float, 2048, 2>(tb, a, sm_count, max_ctas, s, info, query_only);
         case 3: return fused_go<float, 2048, 3>(tb, a, sm_count, max_ctas, s, info, query_only);
-        default: return a.trace_every > 0 ? fused_go<float, 2048, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+        default: return tb.potential == 1 ? fused_go<float, 2048, 5>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : a.trace_every > 0 ? fused_go<float, 2048, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
                                   : fused_go<float, 2048, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
         }
     case 4096:
@@ -24,7 +26,8 @@ cudaError_t fused_launch_f32_b(int N, const Tables<float> &tb, const LaunchArgs 
         case 1: return fused_go<float, 4096, 1>(tb, a, sm_count, max_ctas, s, info, query_only);
         case 2: return fused_go<float, 4096, 2>(tb, a, sm_count, max_ctas, s, info, query_only);
         case 3: return fused_go<float, 4096, 3>(tb, a, sm_count, max_ctas, s, info, query_only);
-        default: return a.trace_every > 0 ? fused_go<float, 4096, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+        default: return tb.potential == 1 ? fused_go<float, 4096, 5>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : a.trace_every > 0 ? fused_go<float, 4096, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
                                   : fused_go<float, 4096, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
         }
     default: return fused_launch_f32_c(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);

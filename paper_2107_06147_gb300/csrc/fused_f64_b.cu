@@ -9,11 +9,14 @@ cudaError_t fused_launch_f64_c(int N, const Tables<double> &tb, const LaunchArgs
 cudaError_t fused_launch_f64_b(int N, const Tables<double> &tb, const LaunchArgs &a, int sm_count, int max_ctas,
                              cudaStream_t s, FusedInfo *info, bool query_only, int variant)
 {
-    if (a.trace_every > 0) variant = 0;   // the per-step summary runs the traced twin of variant 0
+    // the per-step summary runs the traced twin of variant 0, the KSU potential its own twin of it
+    if (a.trace_every > 0 || tb.potential == 1) variant = 0;
     switch (N) {
-    case 2048: return a.trace_every > 0 ? fused_go<double, 2048, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+    case 2048: return tb.potential == 1 ? fused_go<double, 2048, 5>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : a.trace_every > 0 ? fused_go<double, 2048, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
                                   : fused_go<double, 2048, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
-    case 4096: return a.trace_every > 0 ? fused_go<double, 4096, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
+    case 4096: return tb.potential == 1 ? fused_go<double, 4096, 5>(tb, a, sm_count, max_ctas, s, info, query_only)
+                                  : a.trace_every > 0 ? fused_go<double, 4096, 4>(tb, a, sm_count, max_ctas, s, info, query_only)
                                   : fused_go<double, 4096, 0>(tb, a, sm_count, max_ctas, s, info, query_only);
     default: return fused_launch_f64_c(N, tb, a, sm_count, max_ctas, s, info, query_only, variant);
     }

@@ -387,7 +387,24 @@ template <typename T> struct Tables {
     int ic_cplx;
     const double *prof;    // profile store: (tau, T) pairs of the tabulated media
     double r1s;            // <1S|r|1S> on the grid (discrete), the unit of the summary's R
+    // the isotropic KSU potential (potential = 1; App. E), see qtraj_params.potential:
+    int potential;
+    const T *phi_tab;      // (phi, h phi') at a = KSU_PHI_A0 + i h, i < KSU_PHI_NODES (h = 1/KSU_PHI_PER)
+    const T *phi_ser;      // [KSU_PHI_SER][2]: the small-argument series of phi, coefficients of y^k
+                           // (y = a^2) of the ln a part and of the rest (k = 1 ..)
+    T ksu_a_dr;            // a / dr: the Coulomb part a/r = ksu_a_dr / j
+    T ksu_sig_dr;          // sigma dr: the linear part sigma r = ksu_sig_dr j
+    T ksu_two_sigma;       // 2 sigma
+    T ksu_cap;             // V_vac(r_SB) = -a/r_SB + sigma r_SB
+    T ksu_alpha0, ksu_b0, ksu_mu0sq;   // alpha_s(mu) = alpha0 / (1 + alpha0 b0 ln(mu^2 / mu0^2))
+    T ksu_md2;             // F_mD^2 Nc (1 + N_F/6) pi C_F: m_D^2 = ksu_md2 T^2 alpha_s(2 pi T)
+    T ksu_cf;              // C_F
+    T ksu_dt;              // the step (GeV^-1) in the working precision
 };
+constexpr double KSU_PHI_A0 = 0.5, KSU_PHI_A1 = 40.0;
+constexpr int KSU_PHI_PER = 256;                                   // nodes per unit of a
+constexpr int KSU_PHI_NODES = (int)((KSU_PHI_A1 - KSU_PHI_A0) * KSU_PHI_PER) + 1;
+constexpr int KSU_PHI_SER = 8;                                     // series terms (a < KSU_PHI_A0)
 
 // per-launch arguments of both forms
 struct LaunchArgs {

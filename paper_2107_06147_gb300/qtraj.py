@@ -32,7 +32,7 @@ class Params(C.Structure):
     _fields_ = [("alpha_s", C.c_double), ("Nc", C.c_double), ("deriv_type", C.c_int), ("max_jumps", C.c_int),
                 ("r_max", C.c_double), ("l_cap", C.c_int), ("use_rmin", C.c_int), ("precision", C.c_int),
                 ("form", C.c_int), ("save_states", C.c_int), ("variant", C.c_int), ("t_vacuum", C.c_double),
-                ("basis", C.c_int)]
+                ("basis", C.c_int), ("potential", C.c_int), ("ksu_mD_factor", C.c_double)]
 
 
 class InitSpec(C.Structure):
@@ -166,10 +166,13 @@ class Config:
     variant: int = 0
     t_vacuum: float = 0.0
     basis: int = 0
+    potential: int = 0           # 0: OQS+pNRQCD with jumps (App. E); 1: isotropic KSU, no jumps
+    ksu_mD_factor: float = 1.0
 
     def params(self) -> Params:
         return Params(self.alpha_s, self.Nc, self.deriv_type, self.max_jumps, self.r_max, self.l_cap, self.use_rmin,
-                      self.precision, self.form, self.save_states, self.variant, self.t_vacuum, self.basis)
+                      self.precision, self.form, self.save_states, self.variant, self.t_vacuum, self.basis,
+                      self.potential, self.ksu_mD_factor)
 
 
 def fma_peak(precision=FP32) -> float:

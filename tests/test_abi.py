@@ -55,4 +55,4 @@ def test_record_layouts_agree():
     from paper_2107_06147_gb300 import qtraj
     assert qtraj.OBS_DTYPE.itemsize == 192
     assert oracle.OBS_DTYPE.names == qtraj.OBS_DTYPE.names
-    assert ctypes.sizeof(qtraj.Params) == 72 and ctypes.sizeof(qtraj.Medium) == 56
+    assert ctypes.sizeof(qtraj.Params) == 80 and ctypes.sizeof(qtraj.Medium) == 56
