@@ -289,7 +289,8 @@ qtraj_status qtraj_period_draws(const uint64_t *d_seed, const uint32_t *d_k, int
  *     first served while the trajectories admitted and not yet returned stay within
  *     max_inflight_traj (a request larger than the whole budget is admitted when nothing else is in
  *     flight); and fills every idle slot with up to waves_per_launch waves (SMs x resident CTAs)
- *     of trajectories taken in order across the admitted requests of that grid size.  So the
+ *     of trajectories taken across the admitted requests of that grid size in the order `order`
+ *     sets (arrival, or least work first).  So the
  *     trajectories of several requests share a launch, a request that arrives while others run
  *     joins the next launch that frees up, and slots of different grid sizes run concurrently on the
  *     device.  It writes to done_ids the ids of requests whose last trajectory has finished (at
@@ -325,7 +326,21 @@ typedef struct {
     int slots_per_n;               /* contexts per grid size, >= 1 */
     int waves_per_launch;          /* >= 1 */
     int64_t max_inflight_traj;     /* admission budget, >= 1 */
+    int order;                     /* which admitted trajectories of a grid size fill a launch first:
+                                      QTRAJ_ORDER_ARRIVAL (0, requests in arrival order) or
+                                      QTRAJ_ORDER_SHORTEST (1, requests of least work first, the work
+                                      of a request being sum N log2 N x steps of its trajectories;
+                                      ties in arrival order) */
 } qtraj_server_config;
+#define QTRAJ_ORDER_ARRIVAL 0
+#define QTRAJ_ORDER_SHORTEST 1
+
+/* One launch of a server slot: its grid size, trajectories and requests, and its device start and end
+ * (events on the slot's stream around the evolve) in ms since qtraj_server_create. */
+typedef struct {
+    int N, n_traj, n_requests, pad;
+    double start_ms, end_ms;
+} qtraj_launch_rec;
 
 #define QTRAJ_SERVER_MAX_SPECS 64
 
@@ -338,6 +353,10 @@ qtraj_status qtraj_poll(qtraj_server *srv, uint64_t *done_ids, int capacity, int
 qtraj_status qtraj_request_result(qtraj_server *srv, uint64_t request_id, qtraj_obs *out, int n);
 /* Requests queued but not admitted, admitted but not finished, and launches in flight. */
 qtraj_status qtraj_server_counts(const qtraj_server *srv, int *waiting, int *admitted, int *launches_in_flight);
+/* The finished launches recorded since the server was created (or since the last call with
+ * clear = 1), oldest first: up to `capacity` records into out (host), *n_written set.  Host only;
+ * a launch is recorded when qtraj_poll retires it. */
+qtraj_status qtraj_server_launch_log(qtraj_server *srv, qtraj_launch_rec *out, int capacity, int *n_written, int clear);
 /* Waits for the launches in flight, then frees everything the server allocated (not d_ws). */
 void qtraj_server_destroy(qtraj_server *srv);
 

@@ -2,6 +2,8 @@
 // "Serving").  Host code only: the device work of a launch is one qtraj_evolve (fused form) plus an
 // asynchronous copy of its records to a pinned buffer, followed by an event that qtraj_poll queries.
 // Nothing here waits for the device except qtraj_server_create and qtraj_server_destroy.
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +50,8 @@ struct Request {
     std::vector<qtraj_traj_desc> desc;
     std::vector<qtraj_obs> out;
     int remaining = 0;
+    double work = 0.0;    // sum over its trajectories of N log2 N x steps (the order QTRAJ_ORDER_SHORTEST)
+    uint64_t seq = 0;     // arrival order
 };
 
 // the trajectories of one request with one grid size, handed out in order
@@ -55,6 +59,8 @@ struct PendingPart {
     uint64_t id;
     std::vector<int> idx;
     size_t next = 0;
+    double work = 0.0;    // of its request
+    uint64_t seq = 0;
 };
 
 // a run of consecutive trajectories of a launch: request id, its descriptor positions idx
@@ -68,6 +74,8 @@ struct Slot {
     int N = 0, cap = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t t_start = nullptr, t_end = nullptr;   // timing events around a launch's evolve
+    int launch_traj = 0;
     qtraj_obs *h_obs = nullptr;
     bool busy = false;
     std::vector<LaunchPart> parts;
@@ -80,7 +88,7 @@ struct Slot {
 struct PerN {
     int N = 0, cap = 0;
     std::vector<Slot> slots;
-    std::deque<PendingPart> pending;
+    std::deque<PendingPart> pending;   // arrival order; QTRAJ_ORDER_SHORTEST picks the least work first
 };
 
 bool valid_n(int N) { return N >= 16 && N <= 16384 && (N & (N - 1)) == 0; }
@@ -99,6 +107,8 @@ qtraj_status check_config(const qtraj_server_config *c)
         return failf(QTRAJ_EINVAL, "n_specs must be in [1, %d]", QTRAJ_SERVER_MAX_SPECS);
     if (c->slots_per_n <= 0 || c->waves_per_launch <= 0 || c->max_inflight_traj <= 0)
         return failf(QTRAJ_EINVAL, "slots_per_n, waves_per_launch and max_inflight_traj must be positive");
+    if (c->order != QTRAJ_ORDER_ARRIVAL && c->order != QTRAJ_ORDER_SHORTEST)
+        return failf(QTRAJ_EINVAL, "order must be QTRAJ_ORDER_ARRIVAL or QTRAJ_ORDER_SHORTEST");
     return QTRAJ_OK;
 }
 
@@ -138,6 +148,9 @@ struct qtraj_server {
     std::deque<uint64_t> done;                   // finished, not yet reported by qtraj_poll
     int64_t inflight = 0;                        // trajectories of admitted, unreturned requests
     int admitted = 0;
+    uint64_t seq = 0;                            // arrival counter
+    cudaEvent_t epoch = nullptr;                 // recorded at creation: the zero of the launch log
+    std::vector<qtraj_launch_rec> log;           // finished launches
 };
 
 extern "C" {
@@ -202,6 +215,7 @@ qtraj_status qtraj_server_create(const qtraj_server_config *cfg, void *d_ws, siz
             if ((st = qt::reserve_media(sl.ctx, pn.cap)) != QTRAJ_OK) break;
             if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreate(&sl.t_start) != cudaSuccess || cudaEventCreate(&sl.t_end) != cudaSuccess ||
                 cudaMallocHost(&sl.h_obs, sizeof(qtraj_obs) * pn.cap) != cudaSuccess) {
                 st = failf(QTRAJ_ECUDA, "stream, event or pinned buffer: %s", cudaGetErrorString(cudaGetLastError()));
                 break;
@@ -212,6 +226,9 @@ qtraj_status qtraj_server_create(const qtraj_server_config *cfg, void *d_ws, siz
             sl.media.reserve(pn.cap);
         }
     }
+    if (st == QTRAJ_OK && (cudaEventCreate(&s->epoch) != cudaSuccess || cudaEventRecord(s->epoch, 0) != cudaSuccess ||
+                           cudaEventSynchronize(s->epoch) != cudaSuccess))
+        st = failf(QTRAJ_ECUDA, "epoch event: %s", cudaGetErrorString(cudaGetLastError()));
     if (st != QTRAJ_OK) {
         qtraj_server_destroy(s.release());
         return st;
@@ -238,6 +255,14 @@ qtraj_status qtraj_submit(qtraj_server *s, const qtraj_traj_desc *traj, int n, u
     r->desc.assign(traj, traj + n);
     r->out.assign(n, qtraj_obs{});
     r->remaining = n;
+    r->seq = s->seq++;
+    for (int t = 0; t < n; ++t) {
+        const qtraj_medium &m = traj[t].medium;
+        // the Bjorken medium's steps, as the engine counts them (work estimate only)
+        const double tau_f = m.tau0 * std::pow(m.T0 / m.Tf, 3.0);
+        const double steps = m.T0 > m.Tf ? std::ceil((tau_f - m.tau0) / (0.1973269804 * s->cfg.dt)) : 0.0;
+        r->work += (double)traj[t].N * std::log2((double)traj[t].N) * steps;
+    }
     s->reqs[request_id] = std::move(r);
     s->waiting.push_back(request_id);
     return QTRAJ_OK;
@@ -248,6 +273,14 @@ namespace {
 // moves the records of a finished launch into their requests
 void collect(qtraj_server *s, Slot &sl)
 {
+    qtraj_launch_rec rec{sl.N, sl.launch_traj, (int)sl.parts.size(), 0, -1.0, -1.0};
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, s->epoch, sl.t_start) == cudaSuccess &&
+        cudaEventElapsedTime(&b, s->epoch, sl.t_end) == cudaSuccess) {
+        rec.start_ms = a;
+        rec.end_ms = b;
+    }
+    s->log.push_back(rec);
     int o = 0;
     for (LaunchPart &p : sl.parts) {
         Request &r = *s->reqs.at(p.id);
@@ -274,7 +307,8 @@ void admit(qtraj_server *s)
         // split by grid size, keeping submission order inside each
         std::map<int, std::vector<int>> byN;
         for (int t = 0; t < (int)n; ++t) byN[r.desc[t].N].push_back(t);
-        for (auto &kv : byN) s->perN[s->n_index.at(kv.first)].pending.push_back(PendingPart{r.id, std::move(kv.second), 0});
+        for (auto &kv : byN)
+            s->perN[s->n_index.at(kv.first)].pending.push_back(PendingPart{r.id, std::move(kv.second), 0, r.work, r.seq});
     }
 }
 
@@ -288,7 +322,12 @@ qtraj_status launch(qtraj_server *s, PerN &pn, Slot &sl)
     std::map<std::tuple<double, double, double, double, double>, int> mkey;
     int n = 0;
     while (!pn.pending.empty() && n < sl.cap) {
-        PendingPart &pp = pn.pending.front();
+        // the next part: the front (arrival order), or the one of least work
+        auto it_pp = pn.pending.begin();
+        if (s->cfg.order == QTRAJ_ORDER_SHORTEST)
+            for (auto i2 = pn.pending.begin(); i2 != pn.pending.end(); ++i2)
+                if (i2->work < it_pp->work || (i2->work == it_pp->work && i2->seq < it_pp->seq)) it_pp = i2;
+        PendingPart &pp = *it_pp;
         const Request &r = *s->reqs.at(pp.id);
         LaunchPart lp{pp.id, {}};
         while (pp.next < pp.idx.size() && n < sl.cap) {
@@ -311,14 +350,17 @@ qtraj_status launch(qtraj_server *s, PerN &pn, Slot &sl)
             ++n;
         }
         sl.parts.push_back(std::move(lp));
-        if (pp.next == pp.idx.size()) pn.pending.pop_front();
+        if (pp.next == pp.idx.size()) pn.pending.erase(it_pp);
     }
     if (n == 0) return QTRAJ_OK;
     SOK(qtraj_set_spec_idx(sl.ctx, sl.spec_idx.data(), n));
+    SCK(cudaEventRecord(sl.t_start, sl.stream));
     SOK(qtraj_evolve(sl.ctx, n, sl.media.data(), (int)sl.media.size(), sl.medium_idx.data(), sl.seeds.data(),
                      (void *)sl.stream));
+    SCK(cudaEventRecord(sl.t_end, sl.stream));
     SOK(qt::obs_to_host_async(sl.ctx, sl.h_obs, sl.stream));
     SCK(cudaEventRecord(sl.done, sl.stream));
+    sl.launch_traj = n;
     sl.busy = true;
     return QTRAJ_OK;
 }
@@ -382,6 +424,17 @@ qtraj_status qtraj_server_counts(const qtraj_server *s, int *waiting, int *admit
     return QTRAJ_OK;
 }
 
+qtraj_status qtraj_server_launch_log(qtraj_server *s, qtraj_launch_rec *out, int capacity, int *n_written, int clear)
+{
+    qt::api_clear_error();
+    if (!s || !n_written || capacity < 0 || (capacity > 0 && !out)) return failf(QTRAJ_EINVAL, "bad argument");
+    const int n = (int)std::min<size_t>((size_t)capacity, s->log.size());
+    if (n) std::memcpy(out, s->log.data(), sizeof(qtraj_launch_rec) * n);
+    *n_written = n;
+    if (clear) s->log.clear();
+    return QTRAJ_OK;
+}
+
 void qtraj_server_destroy(qtraj_server *s)
 {
     if (!s) return;
@@ -391,8 +444,11 @@ void qtraj_server_destroy(qtraj_server *s)
             if (sl.ctx) qtraj_destroy(sl.ctx);
             if (sl.h_obs) cudaFreeHost(sl.h_obs);
             if (sl.done) cudaEventDestroy(sl.done);
+            if (sl.t_start) cudaEventDestroy(sl.t_start);
+            if (sl.t_end) cudaEventDestroy(sl.t_end);
             if (sl.stream) cudaStreamDestroy(sl.stream);
         }
+    if (s->epoch) cudaEventDestroy(s->epoch);
     delete s;
 }
 

@@ -63,7 +63,15 @@ class TrajDesc(C.Structure):
 class ServerConfig(C.Structure):
     _fields_ = [("Ns", C.POINTER(C.c_int)), ("n_N", C.c_int), ("dr", C.c_double), ("dt", C.c_double),
                 ("M", C.c_double), ("params", C.POINTER(Params)), ("specs", C.POINTER(InitSpec)), ("n_specs", C.c_int),
-                ("slots_per_n", C.c_int), ("waves_per_launch", C.c_int), ("max_inflight_traj", C.c_int64)]
+                ("slots_per_n", C.c_int), ("waves_per_launch", C.c_int), ("max_inflight_traj", C.c_int64),
+                ("order", C.c_int)]
+
+
+ORDER_ARRIVAL, ORDER_SHORTEST = 0, 1
+
+# qtraj_launch_rec: one finished launch of a server slot
+LAUNCH_DTYPE = np.dtype([("N", "<i4"), ("n_traj", "<i4"), ("n_requests", "<i4"), ("pad", "<i4"),
+                         ("start_ms", "<f8"), ("end_ms", "<f8")])
 
 
 # qtraj_traj_desc as a numpy record, to build large requests without a Python loop
@@ -110,6 +118,7 @@ _PROTOS = {
     "qtraj_request_result": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int]),
     "qtraj_server_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "qtraj_server_destroy": (None, [C.c_void_p]),
+    "qtraj_server_launch_log": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "qtraj_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_period_draws": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_evolve_static": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(InitSpec), C.c_int, C.POINTER(C.c_int),

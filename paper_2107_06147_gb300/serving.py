@@ -4,8 +4,8 @@ The scheduler is native (include/qtraj.h, "Serving"; csrc/serve.cu): for every g
 server keeps a few engine slots (a context with its share of the workspace, its own CUDA stream and
 a pinned result buffer).  qtraj_poll never blocks: it retires finished launches, admits queued
 requests first come first served within a budget of trajectories in flight, and fills every idle
-slot with up to `wave_mult` waves of trajectories taken in order across the admitted requests of that
-N -- trajectories of several requests share a launch, a request that arrives while others run joins
+slot with up to `wave_mult` waves of trajectories taken across the admitted requests of that N in
+arrival order or least work first (`order`) -- trajectories of several requests share a launch, a request that arrives while others run joins
 the next launch that frees up, and slots of different N run concurrently on the device.
 
 Each trajectory's result depends only on its own inputs (initial state, medium, seed), never on the
@@ -60,7 +60,7 @@ class Server:
 
     def __init__(self, Ns=(1024, 2048, 4096, 8192, 16384), slots_per_n: int = 2, precision=qtraj.FP32,
                  max_inflight_traj: int = 1 << 20, dr: float = 5.0 / 512, dt: float = 0.001, wave_mult: int = 1,
-                 specs=INIT_SPECS, cfg: qtraj.Config | None = None):
+                 specs=INIT_SPECS, cfg: qtraj.Config | None = None, order: int = qtraj.ORDER_ARRIVAL):
         import torch
         self.lib = qtraj.load()
         base = cfg or qtraj.Config(precision=precision)
@@ -68,7 +68,7 @@ class Server:
         self._Ns = (C.c_int * len(Ns))(*Ns)
         self._specs = (qtraj.InitSpec * len(specs))(*specs)
         self._cfg = qtraj.ServerConfig(self._Ns, len(Ns), dr, dt, base.M, C.pointer(self._params), self._specs,
-                                       len(specs), slots_per_n, wave_mult, max_inflight_traj)
+                                       len(specs), slots_per_n, wave_mult, max_inflight_traj, order)
         nb = C.c_size_t()
         qtraj._check(self.lib.qtraj_server_workspace_bytes(C.byref(self._cfg), C.byref(nb)))
         self.ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
@@ -106,6 +106,14 @@ class Server:
         w, a, l = C.c_int(), C.c_int(), C.c_int()
         qtraj._check(self.lib.qtraj_server_counts(self.h, C.byref(w), C.byref(a), C.byref(l)))
         return w.value, a.value, l.value
+
+    def launch_log(self, clear: bool = False) -> np.ndarray:
+        """The finished launches (grid size, trajectories, requests, device start/end in ms)."""
+        out = np.zeros(4096, dtype=qtraj.LAUNCH_DTYPE)
+        n = C.c_int()
+        qtraj._check(self.lib.qtraj_server_launch_log(self.h, C.c_void_p(out.ctypes.data), len(out), C.byref(n),
+                                                      1 if clear else 0))
+        return out[: n.value].copy()
 
     def idle(self) -> bool:
         return not self.requests and self.counts() == (0, 0, 0)

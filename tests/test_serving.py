@@ -15,7 +15,8 @@ def _cfg(qtraj, Ns, specs, **kw):
     ns = (C.c_int * len(Ns))(*Ns)
     sp = (qtraj.InitSpec * len(specs))(*specs)
     c = qtraj.ServerConfig(ns, len(Ns), kw.get("dr", 5.0 / 512), kw.get("dt", 0.001), 4.65, C.pointer(p), sp,
-                           kw.get("n_specs", len(specs)), kw.get("slots", 1), kw.get("waves", 1), kw.get("budget", 100))
+                           kw.get("n_specs", len(specs)), kw.get("slots", 1), kw.get("waves", 1), kw.get("budget", 100),
+                           kw.get("order", 0))
     return c, (p, ns, sp)
 
 
@@ -25,7 +26,8 @@ def test_server_arguments_checked_on_host():
     lib = qtraj.load()
     nb = C.c_size_t()
     for Ns, kw, msg in (((100,), {}, b"power of two"), ((64, 64), {}, b"twice"), ((64,), {"n_specs": 0}, b"n_specs"),
-                        ((64,), {"budget": 0}, b"positive"), ((64,), {"dt": 0.0}, b"positive")):
+                        ((64,), {"budget": 0}, b"positive"), ((64,), {"dt": 0.0}, b"positive"),
+                        ((64,), {"order": 2}, b"order")):
         c, keep = _cfg(qtraj, Ns, serving.INIT_SPECS, **kw)
         assert lib.qtraj_server_workspace_bytes(C.byref(c), C.byref(nb)) == 1
         assert msg in lib.qtraj_last_error(None)
@@ -157,3 +159,58 @@ def test_server_errors():
     assert lib.qtraj_request_result(srv.h, 5, C.c_void_p(out.ctypes.data), len(d)) == 0
     assert lib.qtraj_request_result(srv.h, 5, C.c_void_p(out.ctypes.data), len(d)) == 1    # forgotten
     srv.close()
+
+
+@pytest.mark.gpu
+def test_requests_overlap_on_the_device():
+    """Continuous batching, not a queue: two requests of different grid sizes submitted together run
+    on their slots' streams at the same time -- the device intervals of their launches (events around
+    each evolve, qtraj_server_launch_log) overlap -- and each result is the same as alone."""
+    _gpu()
+    from paper_2107_06147_gb300 import qtraj, serving
+    srv = serving.Server(Ns=(256, 512), slots_per_n=1, precision=qtraj.FP32, wave_mult=1)
+    a = serving.Request(rid=1, N=256, init=0, T0=0.45, kappa_hat=4.0, gamma_hat=-1.0, ntraj=3000, seed0=0, Tf=0.3)
+    b = serving.Request(rid=2, N=512, init=2, T0=0.45, kappa_hat=4.0, gamma_hat=-1.0, ntraj=1500, seed0=10 ** 6, Tf=0.3)
+    srv.run_stream([a, b], [0.0, 0.0])
+    log = srv.launch_log()
+    srv.close()
+    assert set(log["N"]) == {256, 512} and (log["end_ms"] > log["start_ms"]).all()
+    la, lb = log[log["N"] == 256], log[log["N"] == 512]
+    overlap = min(la["end_ms"].max(), lb["end_ms"].max()) - max(la["start_ms"].min(), lb["start_ms"].min())
+    span = max(la["end_ms"].max(), lb["end_ms"].max()) - min(la["start_ms"].min(), lb["start_ms"].min())
+    assert overlap > 0.5 * min(la["end_ms"].max() - la["start_ms"].min(), lb["end_ms"].max() - lb["start_ms"].min()), log
+    assert span > 0
+    for r in (a, b):
+        ref = _direct(qtraj, r.N, qtraj.FP32, serving.INIT_SPECS, r.descriptors())
+        for f in qtraj.OBS_DTYPE.names:
+            assert np.array_equal(r.obs[f], ref[f]), (r.rid, f)
+
+
+@pytest.mark.gpu
+def test_shortest_work_first_order():
+    """QTRAJ_ORDER_SHORTEST: of the requests admitted for one grid size, the launch takes those of
+    least work first.  Three requests of one N arrive together, the long one first; with a launch of
+    one wave the short ones finish before it (in arrival order the long one would hold the slot)."""
+    _gpu()
+    from paper_2107_06147_gb300 import qtraj, serving
+    done = {}
+    for order in (qtraj.ORDER_ARRIVAL, qtraj.ORDER_SHORTEST):
+        srv = serving.Server(Ns=(256,), slots_per_n=1, precision=qtraj.FP32, wave_mult=1, order=order)
+        cap = srv.launch_log  # noqa: F841  (the log is read below)
+        reqs = [serving.Request(rid=1, N=256, init=0, T0=0.5, kappa_hat=4.0, gamma_hat=-1.0, ntraj=6000, seed0=0,
+                                Tf=0.25),
+                serving.Request(rid=2, N=256, init=1, T0=0.35, kappa_hat=4.0, gamma_hat=-1.0, ntraj=64, seed0=10 ** 6,
+                                Tf=0.3),
+                serving.Request(rid=3, N=256, init=2, T0=0.35, kappa_hat=4.0, gamma_hat=-1.0, ntraj=64, seed0=2 * 10 ** 6,
+                                Tf=0.3)]
+        srv.run_stream(reqs, [0.0, 0.0, 0.0])
+        srv.close()
+        done[order] = {r.rid: r.done_time for r in reqs}
+        for r in reqs[1:]:
+            ref = _direct(qtraj, 256, qtraj.FP32, serving.INIT_SPECS, r.descriptors())
+            for f in qtraj.OBS_DTYPE.names:
+                assert np.array_equal(r.obs[f], ref[f]), (order, r.rid, f)
+    s = done[qtraj.ORDER_SHORTEST]
+    assert s[2] < s[1] and s[3] < s[1]
+    a = done[qtraj.ORDER_ARRIVAL]
+    assert a[1] <= a[2] and a[1] <= a[3]
