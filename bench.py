@@ -6,9 +6,10 @@ N = 4096, L = 40 GeV^-1, dt = 0.001 GeV^-1, M = 4.65 GeV, alpha_s = 0.3, Bjorken
 0.425 GeV at 0.6 fm/c to 0.25 GeV (11,899 steps): 180,000 trajectories.  Trajectory t has initial
 state t % 3, medium (t // 3) % 6 and seed t; bench step i evolves the i-th slice of `--batch` of them
 (a multiple of 18, so every slice has the same pattern of (initial state, medium) pairs) through its
-whole medium: one qtraj_evolve, i.e. the no-jump run of each of the 18 groups, then every
-trajectory.  The metric counts executed trajectory-steps only (rMin short-cuts count zero, the
-no-jump runs count).
+whole medium: one qtraj_evolve, i.e. one launch of the fused kernel whose first work items are the
+no-jump runs of the 18 groups.  The metric counts executed trajectory-steps only (rMin short-cuts
+count zero, the no-jump runs count, and so does a trajectory taken up before its group's p_NoJump
+was known, which runs its whole medium).
 
 Timing: W warm-up steps, then exactly K steps between a barrier + synchronize on both sides,
 measured with CUDA events on the launching stream; the maximum over ranks is reported.  A 256 MiB
@@ -41,7 +42,7 @@ UNIT = "traj-steps/s"
 N_GRID, L_BOX, DT = 4096, 40.0, 0.001
 # DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture of the current
 # kernel source (None until the kernel has been captured again after a change)
-PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 7.71
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = None
 N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
@@ -222,11 +223,16 @@ def run_ours(args):
     value = total_steps / (ms / 1e3)
     e2e_value = total_steps / (e2e_ms / 1e3)
 
-    # roofline of the dominant kernel (the fused FP32 kernel, main launch): algorithmic flops of the
-    # executed trajectory-steps of this rank over that kernel's event time
-    main_steps = steps_exec  # includes the short no-jump launches, < 0.2% of the steps
+    # roofline of the dominant kernel (the fused FP32 kernel; one launch per step, the groups' no-jump
+    # runs included): the nominal flops of the odd-extended length-2N transform pair, 10 (2N)
+    # log2(2N) + pointwise = 1,187,840 per trajectory-step at N = 4096, over that kernel's event time,
+    # against the FP32 FMA peak from unit counts (SMs x 128 lanes x 2 flops x 2070 MHz); the flops the
+    # implementation needs (an N-point FFT per sine transform, half the nominal) go beside it
+    main_steps = steps_exec
+    nominal = nominal_flops_per_step(N_GRID)
     alg = algorithmic_flops_per_step(N_GRID)
-    achieved = main_steps * alg / (sum(main_ms) / 1e3) / 1e12
+    achieved = main_steps * nominal / (sum(main_ms) / 1e3) / 1e12
+    achieved_alg = main_steps * alg / (sum(main_ms) / 1e3) / 1e12
     peak = fp32_peak_tflops(kinfo.sm_count)
     # DRAM bytes of one main launch: the per-trajectory-step figure of the ncu capture of this kernel
     # (dram__bytes_read.sum + dram__bytes_write.sum over 456 trajectories x 1000 steps) scaled to the
@@ -236,13 +242,15 @@ def run_ours(args):
         traffic = round(PROFILED_DRAM_BYTES_PER_TRAJ_STEP * main_steps / args.steps)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_note": "bytes per launch, scaled from a 456-trajectory x 1000-step ncu capture",
-                "flops_per_traj_step": alg, "nominal_fft_equivalent_flops_per_traj_step": nominal_flops_per_step(N_GRID),
-                "peak_note": "FP32 FMA peak from unit counts: SMs x 128 lanes x 2 flops x 2070 MHz (not measured)"}
+                "traffic_note": "DRAM bytes per launch, scaled from an ncu capture of this kernel (608 trajectories x 300 steps)",
+                "flops_per_traj_step": nominal,
+                "flops_note": "nominal 10 (2N) log2(2N) + 30 N of the odd-extended transform pair",
+                "algorithmic_flops_per_traj_step": alg, "algorithmic_tflops": round(achieved_alg, 3),
+                "algorithmic_frac": round(achieved_alg / peak, 4),
+                "peak_note": "FP32 FMA peak from unit counts: SMs x 128 lanes x 2 flops x 2070 MHz"}
     if rank == 0:
         fma = qtraj.fma_peak(qtraj.FP32)
-        roofline["fma_peak_measured_tflops"] = round(fma, 2)
-        roofline["frac_of_measured_fma"] = round(achieved / fma, 4)
+        roofline["fma_rate_measured_tflops"] = round(fma, 2)   # context: an FMA microbenchmark on this GPU
 
     result = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
@@ -262,9 +270,15 @@ def run_ours(args):
     # the comparison forms, the CPU baseline and serving are single-GPU measurements: with N > 1 they
     # would hold every GPU at the final barrier, so they run at N = 1 only
     if rank == 0 and world == 1 and not args.no_compare:
-        result["plain_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.PLAIN, args.compare_batch)
-        result["fused_fp64"] = measure_form(qtraj, w, specs, media, qtraj.FP64, qtraj.FUSED, args.compare_batch)
+        # the FP64 forms at two batch sizes, to show that their throughput has plateaued at the
+        # smaller one (the speed-up is quoted against the larger)
+        for k, form in (("plain_fp64", qtraj.PLAIN), ("fused_fp64", qtraj.FUSED)):
+            small = measure_form(qtraj, w, specs, media, qtraj.FP64, form, args.compare_batch // 4)
+            result[k] = measure_form(qtraj, w, specs, media, qtraj.FP64, form, args.compare_batch)
+            result[k]["value_at_quarter_batch"] = small["value"]
         result["speedup_vs_plain_fp64"] = round(value / world / result["plain_fp64"]["value"], 2)
+        result["speedup_note"] = (f"fused FP32 at {B} trajectories per step against the plain FP64 form at "
+                                  f"{args.compare_batch}")
         # the FP64 forms are bound by GB300's FP64 pipe: their algorithmic rate against the FP64 FMA
         # throughput measured on the same GPU
         fma64 = qtraj.fma_peak(qtraj.FP64)
@@ -321,29 +335,53 @@ def run_uneven(args):
                       "jumps_mean": round(float(obs["n_jumps"].mean()), 2)}))
 
 
+def _serve_once(args, rate_hz, order):
+    """Replays the first --serving-requests requests of the stream, their arrival gaps rescaled from
+    200 req/s to rate_hz, with the given launch order; returns the summary dict."""
+    import torch
+
+    from paper_2107_06147_gb300 import inputs, qtraj, serving
+    st = inputs.serving_prefix(args.serving_requests)
+    arrival = st["arrival_s"] * (200.0 / rate_hz)
+    reqs = serving.requests_from_stream(st)
+    Ns = sorted(set(int(n) for n in st["N"]))
+    srv = serving.Server(Ns=tuple(Ns), slots_per_n=2, wave_mult=4,
+                         order=qtraj.ORDER_SHORTEST if order == "shortest" else qtraj.ORDER_ARRIVAL)
+    torch.cuda.synchronize()
+    wall = srv.run_stream(reqs, arrival)
+    log = srv.launch_log()
+    srv.close()
+    lat = serving.latency_stats(reqs)
+    steps = int(sum(int(r.obs["n_steps_exec"].sum()) for r in reqs))
+    # device concurrency: the fraction of the busy time during which launches of two or more slots ran
+    ev = sorted([(t, +1) for t in log["start_ms"]] + [(t, -1) for t in log["end_ms"]])
+    busy = multi = 0.0
+    depth, last = 0, None
+    for t, d in ev:
+        if last is not None and depth > 0:
+            busy += t - last
+            if depth > 1:
+                multi += t - last
+        depth += d
+        last = t
+    return {"requests": len(reqs), "n_latencies": lat["n"], "order": order, "offered_rate_hz": rate_hz,
+            "latency_p50_s": round(lat["p50_s"], 3), "latency_p99_s": round(lat["p99_s"], 3),
+            "latency_mean_s": round(lat["mean_s"], 3), "latency_max_s": round(lat["max_s"], 3),
+            "wall_s": round(wall, 3), "traj_steps": steps, "traj_steps_per_s": round(steps / wall, 1),
+            "completed_rate_hz": round(len(reqs) / wall, 4), "Ns": Ns, "launches": int(len(log)),
+            "concurrent_fraction": round(multi / busy, 3) if busy > 0 else None,
+            "trajectories": int(sum(r.ntraj for r in reqs)), "precision": "fp32 fused, rMin shortcut off"}
+
+
 def run_serving_sweep(args):
     """The first --serving-requests requests of the stream replayed at each offered rate of
     --serving-sweep (the arrival gaps of the 200 req/s stream rescaled): latency against offered load,
-    down to a rate one GPU sustains.  One JSON line per rate."""
-    import torch
-
-    from paper_2107_06147_gb300 import inputs, serving
+    down to a rate one GPU sustains, for the launch order(s) of --serving-order.  One JSON line per
+    (rate, order)."""
+    orders = ("arrival", "shortest") if args.serving_order == "both" else (args.serving_order,)
     for rate in [float(r) for r in args.serving_sweep.split(",")]:
-        st = inputs.serving_prefix(args.serving_requests)
-        arrival = st["arrival_s"] * (200.0 / rate)
-        reqs = serving.requests_from_stream(st)
-        Ns = sorted(set(int(n) for n in st["N"]))
-        srv = serving.Server(Ns=tuple(Ns), slots_per_n=2, wave_mult=4)
-        torch.cuda.synchronize()
-        wall = srv.run_stream(reqs, arrival)
-        srv.close()
-        lat = serving.latency_stats(reqs)
-        steps = int(sum(int(r.obs["n_steps_exec"].sum()) for r in reqs))
-        print(json.dumps({"serving_sweep": True, "offered_rate_hz": rate, "requests": len(reqs),
-                          "latency_p50_s": round(lat["p50_s"], 3), "latency_p99_s": round(lat["p99_s"], 3),
-                          "latency_mean_s": round(lat["mean_s"], 3), "wall_s": round(wall, 3),
-                          "completed_rate_hz": round(len(reqs) / wall, 4), "traj_steps_per_s": round(steps / wall, 1),
-                          "trajectories": int(sum(r.ntraj for r in reqs)), "traj_steps": steps}), flush=True)
+        for order in orders:
+            print(json.dumps({"serving_sweep": True, **_serve_once(args, rate, order)}), flush=True)
 
 
 def run_serving(args):
@@ -351,24 +389,10 @@ def run_serving(args):
     Poisson request stream (200 req/s, seed 1; initial state in {1S, 2S, 1P}, kappa ~ U[3,7],
     gamma ~ U[-3.5,0], T0 ~ U[0.3,0.6] GeV Bjorken to 0.25 GeV, ntraj log-uniform in [64, 4096],
     N in {1024, ..., 16384} with L = N * 5/512, dt = 0.001).  The offered rate far exceeds one GPU's
-    service rate, so latency includes queueing behind the earlier requests."""
-    import torch
-
-    from paper_2107_06147_gb300 import inputs, serving
-    st = inputs.serving_prefix(args.serving_requests)
-    reqs = serving.requests_from_stream(st)
-    Ns = sorted(set(int(n) for n in st["N"]))
-    srv = serving.Server(Ns=tuple(Ns), slots_per_n=2, wave_mult=4)
-    torch.cuda.synchronize()
-    wall = srv.run_stream(reqs, st["arrival_s"])
-    srv.close()
-    lat = serving.latency_stats(reqs)
-    steps = int(sum(int(r.obs["n_steps_exec"].sum()) for r in reqs))
-    return {"requests": len(reqs), "offered_rate_hz": 200.0, "latency_p50_s": round(lat["p50_s"], 3),
-            "latency_p99_s": round(lat["p99_s"], 3), "latency_mean_s": round(lat["mean_s"], 3),
-            "wall_s": round(wall, 3), "traj_steps": steps, "traj_steps_per_s": round(steps / wall, 1),
-            "completed_rate_hz": round(len(reqs) / wall, 3), "Ns": Ns,
-            "trajectories": int(sum(r.ntraj for r in reqs)), "precision": "fp32 fused, rMin shortcut off"}
+    service rate, so latency includes queueing behind the earlier requests; n_latencies is the number
+    of request latencies the percentiles are taken over."""
+    order = "shortest" if args.serving_order == "shortest" else "arrival"
+    return _serve_once(args, 200.0, order)
 
 
 def measure_form(qtraj, w, specs, media, prec, form, B):
@@ -492,12 +516,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=9216, help="trajectories per bench step (multiple of 18)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--compare-batch", type=int, default=256)
+    ap.add_argument("--compare-batch", type=int, default=1024)
     ap.add_argument("--variant", type=int, default=0, help="fused kernel occupancy variant (0 or 1)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=12)
+    ap.add_argument("--serving-requests", type=int, default=16)
+    ap.add_argument("--serving-order", default="arrival", choices=["arrival", "shortest", "both"],
+                    help="order of the admitted trajectories of a grid size in a launch")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small evolve for a profiler: --batch trajectories, --profile-steps steps")
     ap.add_argument("--profile-steps", type=int, default=1000)
