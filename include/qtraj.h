@@ -256,26 +256,21 @@ typedef struct {
 } qtraj_kernel_info;
 qtraj_status qtraj_kernel_info_get(const qtraj_ctx *ctx, qtraj_kernel_info *out);
 
-/* Measurement (the paper has no counterpart): the FMA throughput of the current device in
- * TFLOP/s (2 flops per fused multiply-add), precision QTRAJ_FP32 or QTRAJ_FP64 -- every thread runs 8
- * independent FMA chains, 8 blocks of 256 threads per SM, best of 3 timed launches after a warm-up.
- * The achievable denominator of a roofline for ALU-bound kernels.  Synchronous; allocates 8 bytes. */
-qtraj_status qtraj_fma_peak(int precision, double *tflops);
-
-/* The generator of the waiting-time algorithm (Sec. 3.2.1, Eq. wta, and the jump choices of
- * Sec. 3.4.2 and Eq. Pl+-; the paper's program calls an unnamed Random()): Philox4x32-10 (Salmon,
- * Moraes, Dror, Shaw, SC'11), computed by the same device code the trajectory kernels run, for
- * checking it against an independent implementation.
- *   qtraj_philox4x32_10: for i < n, the four output words of counter d_ctr[4i .. 4i+3] under key
- *     d_key[2i], d_key[2i+1], into d_out[4i .. 4i+3];
- *   qtraj_period_draws: for i < n, the three uniforms of waiting period d_k[i] of the trajectory
- *     with seed d_seed[i] (counter (k, 0, 0, 0), key = the seed's low and high words): the
- *     threshold r = ((((w1 << 32) | w0) >> 11) + 1/2) 2^-53 and u_l = (w2 + 1/2) 2^-32,
- *     u_c = (w3 + 1/2) 2^-32, into d_out[3i .. 3i+2].
- * All buffers are caller device memory.  Asynchronous on `stream`.  EINVAL for n < 0 or a null
- * buffer with n > 0. */
-qtraj_status qtraj_philox4x32_10(const uint32_t *d_ctr, const uint32_t *d_key, int n, uint32_t *d_out, void *stream);
-qtraj_status qtraj_period_draws(const uint64_t *d_seed, const uint32_t *d_k, int n, double *d_out, void *stream);
+/* Measurement of the radix-16 DFT blocks of the sine transforms (Sec. 3.3; the paper's transforms
+ * are FFTW calls and have no tensor-core form): one CTA per batch of 256 columns of 16 complex FP32
+ * points, resident in shared memory, applies `passes` times y = (F/4) x to every column, F the
+ * 16-point DFT matrix exp(-2 pi i m'm/16) ((F/4)^4 = I).  method 0: CUDA cores (the fused kernel's
+ * DFT16, constants in hi+lo, then times 1/4).  Tensor cores, mma.sync -> FP32 with the matrix in PA
+ * parts, each value in PB parts and the products of part orders j + k <= MAXORD: 1 BF16X3 (BF16,
+ * PA = PB = 2, 3 products); 2 BF16X9 (BF16, PA = 4, PB = 3, 9 products); 3 FP16X3 (FP16, PA = PB = 2,
+ * 3 products); 4 FP16X5 (FP16, PA = 3, PB = 2, 5 products); the FP16 forms scale each column by a
+ * power of two before the split.  x_host: n_batches x 256 x 16 complex values as (re, im) doubles,
+ * point m of column c of batch b at ((b 256 + c) 16 + m), converted to FP32; y_host (same layout)
+ * receives the result; *ms the device time of the timed launch, which follows one untimed launch.
+ * Synchronous; allocates and frees its device buffers.  QTRAJ_EINVAL for a method outside 0..4,
+ * n_batches <= 0, passes < 0 or a null buffer; QTRAJ_ECUDA with the CUDA error's text. */
+qtraj_status qtraj_dft16_study(int method, int n_batches, int passes, const double *x_host, double *y_host,
+                               double *ms);
 
 /* ---------------------------------------------------------------------------------------------
  * Serving: continuous batching of trajectory requests.  (The paper has no counterpart: its program

@@ -119,6 +119,7 @@ _PROTOS = {
     "qtraj_server_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "qtraj_server_destroy": (None, [C.c_void_p]),
     "qtraj_server_launch_log": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "qtraj_dft16_study": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "qtraj_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_period_draws": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "qtraj_evolve_static": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(InitSpec), C.c_int, C.POINTER(C.c_int),
@@ -363,3 +364,17 @@ def period_draws(seeds, k, stream=None):
     _check(load().qtraj_period_draws(C.c_void_p(seeds.data_ptr()), C.c_void_p(k.data_ptr()), n,
                                      C.c_void_p(out.data_ptr()), C.c_void_p(_stream_ptr(stream))))
     return out
+
+
+def dft16_study(method: int, x: np.ndarray, passes: int):
+    """Radix-16 DFT blocks y = (F/4) x on the CUDA cores (method 0) or the tensor cores (1 BF16X3,
+    2 BF16X9, 3 FP16X3, 4 FP16X5), qtraj_dft16_study: x (n_batches, 256, 16) complex, converted to
+    FP32; returns ((F/4)^passes applied to every 16-point column, ms of the timed launch)."""
+    xi = np.ascontiguousarray(x, dtype=np.complex128)
+    if xi.ndim != 3 or xi.shape[1:] != (256, 16):
+        raise ValueError("x must have shape (n_batches, 256, 16)")
+    y = np.zeros_like(xi)
+    ms = C.c_double()
+    _check(load().qtraj_dft16_study(method, xi.shape[0], passes, C.c_void_p(xi.ctypes.data), C.c_void_p(y.ctypes.data),
+                                    C.byref(ms)))
+    return y, ms.value

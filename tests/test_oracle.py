@@ -814,3 +814,16 @@ def test_ksu_evolution_has_no_jumps_and_decays_by_v_i(oracle_lib):
         gam = -2.0 * dr * np.sum(VI * np.abs(uu) ** 2)
         errs.append(abs(rate - gam) / gam)
     assert errs[0] < 1e-5 and 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_dft16_oracle_pins():
+    """The 16-point DFT of oracle/dft16.py: numpy's FFT (a library routine), F^2 = 16 x (m -> -m mod 16),
+    and F^4 = 256 I."""
+    from oracle import dft16 as odft
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((3, 7, 16)) + 1j * rng.standard_normal((3, 7, 16))
+    assert np.allclose(odft.passes(x, 1), np.fft.fft(x, axis=-1), rtol=0, atol=1e-12)
+    rev = x[..., (-np.arange(16)) % 16]
+    assert np.allclose(odft.passes(x, 2), 16 * rev, rtol=0, atol=1e-11)
+    assert np.allclose(odft.passes(x, 4), 256 * x, rtol=0, atol=1e-10)
+    assert np.array_equal(odft.passes(x, 0), x)
