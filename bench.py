@@ -287,6 +287,16 @@ def run_ours(args):
             t = result[k]["value"] * alg / 1e12
             result[k]["tflops"] = round(t, 4)
             result[k]["frac_of_measured_fp64_fma"] = round(t / fma64, 4)
+        # the DFT16 blocks on the tensor cores against the CUDA cores: per-pass rate, the
+        # transform-only ceiling it puts on trajectory-steps/s, and the 64-pass error
+        from paper_2107_06147_gb300 import tcstudy
+        st = tcstudy.run(batches=912, passes=32, reps=2)
+        result["dft16_forms"] = {
+            "note": "radix-16 DFT blocks as CUDA-core butterflies or mma.sync split forms; the ceiling is a "
+                    "step that did nothing but its sine transforms (1536 column-DFTs per trajectory-step)",
+            **{k: {"ns_per_column": v["ns_per_column"],
+                   "transform_only_traj_steps_per_s_ceiling": v["transform_only_traj_steps_per_s_ceiling"],
+                   "rel_err_64pass_rms": v["rel_err_64pass_rms"]} for k, v in st["forms"].items()}}
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(args)
     if rank == 0 and world == 1 and not args.no_serving:
