@@ -15,7 +15,8 @@ Reported per form:
   or with another outcome -- a jump whose threshold lies within a form's rounding of the norm moves
   by a step or two);
 - the largest per-trajectory error on identical jump sequences over the FP32 error model
-  5.5e-8 sqrt(N n_steps) (relative to max(1, S));
+  5.5e-8 sqrt(N n_steps) (relative to max(1, S)), n_steps the steps behind the final state (the
+  whole medium for a trajectory that took the rMin shortcut);
 - the form's throughput on this run.
 """
 from __future__ import annotations
@@ -46,9 +47,16 @@ def _run(w, precision, use_rmin):
                  "traj_steps_per_s": round(s.steps_executed / max(ms / 1e3, 1e-9), 1)}
 
 
+def medium_step_count(T0, tau0, Tf, dt):
+    """Steps of a Bjorken medium from T0 at tau0 down to Tf: ceil((tau_f - tau0) / (hbar c dt)),
+    tau_f = tau0 (T0/Tf)^3 (Sec. 3.4, Table 1)."""
+    return int(np.ceil((tau0 * (T0 / Tf) ** 3 - tau0) / (0.1973269804 * dt)))
+
+
 def run(w, precisions=(qtraj.FP32,), use_rmin: int = 1) -> dict:
     """Runs the workload in FP64 and in each form of `precisions`; returns the report (a dict)."""
     ref, ref_t = _run(w, qtraj.FP64, use_rmin)
+    medium_steps = np.array([medium_step_count(m.T0, m.tau0, m.Tf, w.grid.dt) for m in w.media])
     n = w.n_traj
     sem = ref["surv"].std(axis=0, ddof=1) / np.sqrt(n) if n > 1 else np.zeros(ref["surv"].shape[1])
     report = {"workload": w.name, "trajectories": n, "steps_per_trajectory": int(ref["n_steps_exec"].max()),
@@ -59,6 +67,11 @@ def run(w, precisions=(qtraj.FP32,), use_rmin: int = 1) -> dict:
               "forms": {}}
     for prec in precisions:
         o, t = _run(w, prec, use_rmin)
+        # steps behind each trajectory's final state: a trajectory that took the rMin shortcut on
+        # either side (n_steps_exec = 0) carries its group's no-jump evolution over the whole medium
+        shortcut = ((o["flags"] | ref["flags"]) & qtraj.F_NOJUMP_SHORTCUT) != 0
+        model_steps = np.where(shortcut, medium_steps[w.medium_idx],
+                               np.maximum(np.maximum(o["n_steps_exec"], ref["n_steps_exec"]), 1)).astype(np.float64)
         # identical jump sequences: every jump at the same step with the same outcome (jump digests)
         same = (o["jump_digest"] == ref["jump_digest"]) & (o["n_jumps"] == ref["n_jumps"]) & \
                (o["l"] == ref["l"]) & (o["color"] == ref["color"])
@@ -75,7 +88,7 @@ def run(w, precisions=(qtraj.FP32,), use_rmin: int = 1) -> dict:
             "fraction_jump_steps_differ": float(1.0 - same.mean()),
             "max_traj_error_same_jumps_over_model": (
                 float((d[same].max(axis=1) / np.maximum(1.0, np.abs(ref["surv"][same]).max(axis=1)) /
-                       (5.5e-8 * np.sqrt(w.grid.N * np.maximum(ref["n_steps_exec"][same], 1)))).max())
+                       (5.5e-8 * np.sqrt(w.grid.N * model_steps[same]))).max())
                 if same.any() else None),
             "first_jump_shift_steps_when_count_equal": (np.bincount(np.minimum(shift, 10)).tolist()
                                                         if len(shift) else []),
