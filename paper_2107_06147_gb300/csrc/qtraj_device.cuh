@@ -75,16 +75,20 @@ template <> struct Prec<double> {
 };
 template <> struct Prec<float> {
     struct alignas(16) C { float rh, ih, rl, il; };
-    // The sine pre-factors sin(pi j / N) are single FP32: without their low parts the paired
-    // FP32/FP64 study measured ensemble errors of 8.9e-6 / 6.6e-6 at N = 8192 / 4096 (4.2e-6 /
-    // 2.6e-6 with them), and the 4-byte table is 2.5-3.5% faster at N = 4096 .. 16384.
-    using Rl = float;
+    // The sine pre-factors keep their low parts: rounded to single FP32 they passed the paired
+    // ensemble study (8.9e-6 / 6.6e-6 at N = 8192 / 4096) and ran 2.5-3.5% faster, but the same
+    // rounding every step biased the no-jump norm by +1.3e-8 per step at N = 64.
+    struct alignas(8) Rl { float h, l; };
     static __host__ C make(double re, double im)
     {
         const float rh = (float)re, ih = (float)im;
         return {rh, ih, (float)(re - (double)rh), (float)(im - (double)ih)};
     }
-    static __host__ Rl make_r(double v) { return (float)v; }
+    static __host__ Rl make_r(double v)
+    {
+        const float h = (float)v;
+        return {h, (float)(v - (double)h)};
+    }
     static __device__ __forceinline__ cpx<float> mul(cpx<float> x, C w)
     {
         const float lr = fmaf(x.x, w.rl, -x.y * w.il), li = fmaf(x.x, w.il, x.y * w.rl);
@@ -93,7 +97,7 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ C conj(C w) { return {w.rh, -w.ih, w.rl, -w.il}; }
     static __device__ __forceinline__ cpx<float> mulr(cpx<float> x, Rl s)
     {
-        return {x.x * s, x.y * s};
+        return {fmaf(x.x, s.h, x.x * s.l), fmaf(x.y, s.h, x.y * s.l)};
     }
     static __device__ __forceinline__ C ld(const C *p)
     {
@@ -102,17 +106,18 @@ template <> struct Prec<float> {
     }
     static __device__ __forceinline__ Rl ldr(const Rl *p)
     {
-        return __ldg(p);
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        return {v.x, v.y};
     }
     static __device__ __forceinline__ C from_double(double re, double im)
     {
         const float rh = (float)re, ih = (float)im;
         return {rh, ih, (float)(re - (double)rh), (float)(im - (double)ih)};
     }
-    // The static potential factors are kept without low parts too: the paired FP32/FP64 study
-    // measured ensemble errors of 1.6e-6 / 1.1e-5 at N = 4096 / 8192 (2.6e-6 / 4.2e-6 with hi+lo;
-    // median norm error 6.7e-7 against 5.3e-7), and their table is the one a trajectory reads per
-    // (colour, l) row -- half the bytes.
+    // The static potential factors are the one family of constants kept without low parts: the
+    // paired FP32/FP64 study measured no loss from rounding them (ensemble errors 1.6e-6 / 1.1e-5 at
+    // N = 4096 / 8192 against 2.6e-6 / 4.2e-6 with hi+lo; median norm error 6.7e-7 against 5.3e-7),
+    // while their table is the one a trajectory reads per (colour, l) row -- half the bytes.
     using S = cpx<float>;
     static __host__ __device__ S make_s(double re, double im) { return {(float)re, (float)im}; }
     static __device__ __forceinline__ S ld_s(const S *p) { return ldg(p); }
