@@ -40,9 +40,12 @@ sys.path.insert(0, ROOT)
 METRIC = "traj-steps/s at N=4096 vs plain FP64 GPU form at stated error; p99 request latency"
 UNIT = "traj-steps/s"
 N_GRID, L_BOX, DT = 4096, 40.0, 0.001
-# DRAM bytes per trajectory-step of fused_kernel<float, 4096, 0> in its ncu capture of the current
-# kernel source (None until the kernel has been captured again after a change)
-PROFILED_DRAM_BYTES_PER_TRAJ_STEP = None
+# DRAM traffic of fused_kernel<float, 4096, 0> from two ncu captures of the current kernel source
+# (608 trajectories through 300 and through 1000 steps; dram__bytes_read.sum + dram__bytes_write.sum):
+# a launch costs a fixed part (the first touch of the tables) plus a part per trajectory-step (the
+# per-step tables that fall out of L2).  None until the kernel has been captured again after a change.
+PROFILED_DRAM_FIXED_BYTES = 1.345e6
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 1.875
 N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
@@ -234,15 +237,14 @@ def run_ours(args):
     achieved = main_steps * nominal / (sum(main_ms) / 1e3) / 1e12
     achieved_alg = main_steps * alg / (sum(main_ms) / 1e3) / 1e12
     peak = fp32_peak_tflops(kinfo.sm_count)
-    # DRAM bytes of one main launch: the per-trajectory-step figure of the ncu capture of this kernel
-    # (dram__bytes_read.sum + dram__bytes_write.sum over 456 trajectories x 1000 steps) scaled to the
-    # launch's trajectory-steps
+    # DRAM bytes of one main launch from the two captures: fixed part + per-trajectory-step part x the
+    # launch's executed trajectory-steps
     traffic = None
     if args.precision == "fp32" and args.variant == 0 and PROFILED_DRAM_BYTES_PER_TRAJ_STEP is not None:
-        traffic = round(PROFILED_DRAM_BYTES_PER_TRAJ_STEP * main_steps / args.steps)
+        traffic = round(PROFILED_DRAM_FIXED_BYTES + PROFILED_DRAM_BYTES_PER_TRAJ_STEP * main_steps / args.steps)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_note": "DRAM bytes per launch, scaled from an ncu capture of this kernel (608 trajectories x 300 steps)",
+                "traffic_note": "DRAM bytes per launch: fixed + per-trajectory-step parts from ncu captures of this kernel (608 trajectories x 300 and x 1000 steps)",
                 "flops_per_traj_step": nominal,
                 "flops_note": "nominal 10 (2N) log2(2N) + 30 N of the odd-extended transform pair",
                 "algorithmic_flops_per_traj_step": alg, "algorithmic_tflops": round(achieved_alg, 3),
@@ -270,15 +272,16 @@ def run_ours(args):
     # the comparison forms, the CPU baseline and serving are single-GPU measurements: with N > 1 they
     # would hold every GPU at the final barrier, so they run at N = 1 only
     if rank == 0 and world == 1 and not args.no_compare:
-        # the FP64 forms at two batch sizes, to show that their throughput has plateaued at the
-        # smaller one (the speed-up is quoted against the larger)
+        # the FP64 forms at two batch sizes, to show whether their throughput has plateaued; the
+        # speed-up is quoted against the faster of the two plain FP64 rates
         for k, form in (("plain_fp64", qtraj.PLAIN), ("fused_fp64", qtraj.FUSED)):
-            small = measure_form(qtraj, w, specs, media, qtraj.FP64, form, args.compare_batch // 4)
             result[k] = measure_form(qtraj, w, specs, media, qtraj.FP64, form, args.compare_batch)
-            result[k]["value_at_quarter_batch"] = small["value"]
-        result["speedup_vs_plain_fp64"] = round(value / world / result["plain_fp64"]["value"], 2)
-        result["speedup_note"] = (f"fused FP32 at {B} trajectories per step against the plain FP64 form at "
-                                  f"{args.compare_batch}")
+            big = measure_form(qtraj, w, specs, media, qtraj.FP64, form, 2 * args.compare_batch)
+            result[k]["value_at_double_batch"] = big["value"]
+        best_plain = max(result["plain_fp64"]["value"], result["plain_fp64"]["value_at_double_batch"])
+        result["speedup_vs_plain_fp64"] = round(value / world / best_plain, 2)
+        result["speedup_note"] = (f"fused FP32 at {B} trajectories per step against the faster plain FP64 rate of "
+                                  f"{args.compare_batch} and {2 * args.compare_batch} trajectories")
         # the FP64 forms are bound by GB300's FP64 pipe: their algorithmic rate against the FP64 FMA
         # throughput measured on the same GPU
         fma64 = qtraj.fma_peak(qtraj.FP64)
