@@ -1,7 +1,8 @@
 """In-project autotuner for the fused kernel's launch variant.
 
-For a grid size N and precision, every variant the library offers (radix 16 with 512 or 640
-resident threads per SM, radix 8 with 768 or 1024) is timed on one full wave of trajectories of
+For a grid size N and precision, every variant the library offers (512 or 640 resident threads
+per SM at the size's own radix -- 8 up to N = 2048, 16 above -- and radix 8 with 768 or 1024) is
+timed on one full wave of trajectories of
 the benchmark medium through its first `steps` steps, and the fastest is recorded, with all measured
 rates and the kernel geometry, in a JSON cache (`_lib/autotune.json` in the package, or the path in
 QTRAJ_AUTOTUNE_CACHE).  `best_variant` reads the cache and falls back to variant 0.

@@ -40,7 +40,10 @@ namespace qt {
 // twice the threads per trajectory, half the registers per thread, one more FFT pass.
 
 template <int N, int V = 0> struct FusedPlan {
-    static constexpr int R = (N <= 32) ? 4 : (N <= 512) ? 8 : (V == 2 || V == 3 ? 8 : 16);
+    // radix 8 up to N = 2048 (passes 8, 16, 8 at N = 1024 and 8, 16, 2, 8 at 2048: +9% each over
+    // radix 16's 16, 4, 16 and 16, 8, 16, whose short middle passes and small CTAs cost more
+    // instructions per point), 16 above
+    static constexpr int R = (N <= 32) ? 4 : (N <= 2048) ? 8 : (V == 2 || V == 3 ? 8 : 16);
     static constexpr int G = N / (2 * R);        // threads per trajectory
     static constexpr int NR = N / R;             // stride of a first/last-pass butterfly
     static constexpr int MID = N / (R * R);      // product of the middle radices

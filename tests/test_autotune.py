@@ -1,5 +1,6 @@
 """Autotuner: picks the fastest variant, records every candidate in its JSON cache, and
-best_variant() reads it back (CPU, with a fake measurement); on a GPU it tunes N = 2048."""
+best_variant() reads it back (CPU, with a fake measurement); on a GPU it tunes N = 4096, where
+the variants span radix 16 and radix 8."""
 import json
 
 import pytest
@@ -25,7 +26,7 @@ def test_tune_on_gpu(tmp_path, monkeypatch):
     from paper_2107_06147_gb300 import autotune, build, qtraj
     build.build()
     monkeypatch.setenv("QTRAJ_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
-    rec = autotune.tune(2048, qtraj.FP32, steps=100)
+    rec = autotune.tune(4096, qtraj.FP32, steps=100)
     assert rec["variant"] in autotune.VARIANTS
     assert all(c["rate"] > 0 for c in rec["candidates"])
     assert {c["radix"] for c in rec["candidates"]} == {8, 16}
