@@ -348,6 +348,36 @@ def run_uneven(args):
                       "jumps_mean": round(float(obs["n_jumps"].mean()), 2)}))
 
 
+def run_ksu(args):
+    """Throughput of the isotropic KSU potential (App. E; no jumps, H_eff evolution of singlets) at
+    N = 4096, L = 40, dt = 0.001: --ksu trajectories of Gaussian 1S and 1P singlets (width 0.2) in the
+    benchmark's Bjorken medium 0.425 -> 0.25 GeV (11,899 steps), m_D factor 1, in the FP32 and FP64
+    fused forms (one untimed evolve first).  One JSON line."""
+    import torch
+
+    from paper_2107_06147_gb300 import qtraj
+    n = args.ksu
+    specs = [qtraj.init_spec("gauss", 0.2, 1, 0, 0), qtraj.init_spec("gauss", 0.2, 2, 1, 0)]
+    idx = (np.arange(n) % 2).astype(np.int32)
+    media = [qtraj.medium(0.425, 0.6, 0.25, 0.0, 0.0)]
+    out = {"ksu": True, "N": N_GRID, "trajectories": n, "medium": "Bjorken 0.425 -> 0.25 GeV, m_D factor 1"}
+    for name, prec in (("fp32", qtraj.FP32), ("fp64", qtraj.FP64)):
+        e = qtraj.Engine(qtraj.Config(N=N_GRID, L=L_BOX, dt=DT, precision=prec, potential=1, ksu_mD_factor=1.0))
+        e.init(specs, n, idx)
+        seeds = np.arange(n, dtype=np.uint64)
+        e.evolve(media, seeds, np.zeros(n, np.int32))
+        torch.cuda.synchronize()
+        e.evolve(media, seeds, np.zeros(n, np.int32))
+        torch.cuda.synchronize()
+        st = e.stats()
+        ki = e.kernel_info()
+        e.close()
+        out[name] = {"traj_steps": int(st.steps_executed), "ms": round(st.ms_main, 1),
+                     "traj_steps_per_s": round(st.steps_executed / (st.ms_main / 1e3), 1),
+                     "ctas_per_sm": ki.ctas_per_sm, "regs": ki.regs_per_thread}
+    print(json.dumps(out))
+
+
 def _serve_once(args, rate_hz, order):
     """Replays the first --serving-requests requests of the stream, their arrival gaps rescaled from
     200 req/s to rate_hz, with the given launch order; returns the summary dict."""
@@ -545,6 +575,8 @@ def main():
                     help="throughput of the uneven-batch workload (NTRAJ trajectories of mixed N, l, lifetime)")
     ap.add_argument("--serving-sweep", default="", metavar="RATES",
                     help="comma-separated offered rates (req/s): replay the --serving-requests prefix at each")
+    ap.add_argument("--ksu", type=int, default=0, metavar="NTRAJ",
+                    help="throughput of the isotropic KSU potential at N=4096 (NTRAJ trajectories, FP32 and FP64)")
     ap.add_argument("--precision-study", type=int, default=0, metavar="NTRAJ",
                     help="paired FP64/FP32 study on NTRAJ trajectories of N=8192, L=80, dt=0.0005 (no timing line)")
     args = ap.parse_args()
@@ -558,6 +590,11 @@ def main():
         from paper_2107_06147_gb300 import build
         build.build()
         run_serving_sweep(args)
+        return
+    if args.ksu:
+        from paper_2107_06147_gb300 import build
+        build.build()
+        run_ksu(args)
         return
     if args.precision_study:
         from paper_2107_06147_gb300 import build, inputs, precision
