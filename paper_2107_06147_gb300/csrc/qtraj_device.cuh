@@ -36,6 +36,24 @@ template <typename T> __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<
 template <typename T> __device__ __forceinline__ cpx<T> scale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
 template <typename T> __device__ __forceinline__ cpx<T> mul_i(cpx<T> a) { return {-a.y, a.x}; }   // i*a
 template <typename T> __device__ __forceinline__ cpx<T> mul_mi(cpx<T> a) { return {a.y, -a.x}; }  // -i*a
+// FP32: complex add, subtract and real scale as packed FP32x2 instructions (sm_100 and later): both
+// components in one instruction, each with the same IEEE rounding as the scalar form (a - b is
+// fma(-1, b, a), exact in the product), so results are bit-identical and the issue slots halve
+template <> __device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b)
+{
+    const float2 r = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    return {r.x, r.y};
+}
+template <> __device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b)
+{
+    const float2 r = __ffma2_rn(make_float2(-1.f, -1.f), make_float2(b.x, b.y), make_float2(a.x, a.y));
+    return {r.x, r.y};
+}
+template <> __device__ __forceinline__ cpx<float> scale(cpx<float> a, float s)
+{
+    const float2 r = __fmul2_rn(make_float2(a.x, a.y), make_float2(s, s));
+    return {r.x, r.y};
+}
 // read-only-cache loads of complex values
 __device__ __forceinline__ cpx<float> ldg(const cpx<float> *p)
 {
@@ -62,6 +80,7 @@ template <> struct Prec<double> {
     static __host__ Rl make_r(double v) { return v; }
     static __device__ __forceinline__ cpx<double> mul(cpx<double> x, C w) { return x * w; }
     static __device__ __forceinline__ C conj(C w) { return {w.x, -w.y}; }
+    static __device__ __forceinline__ cpx<double> mul2(cpx<double> x, C w) { return x * w; }
     static __device__ __forceinline__ cpx<double> mulr(cpx<double> x, Rl s) { return scale(x, s); }
     static __device__ __forceinline__ C ld(const C *p) { return ldg(p); }
     static __device__ __forceinline__ Rl ldr(const Rl *p) { return __ldg(p); }
@@ -93,6 +112,14 @@ template <> struct Prec<float> {
     {
         const float lr = fmaf(x.x, w.rl, -x.y * w.il), li = fmaf(x.x, w.il, x.y * w.rl);
         return {fmaf(x.x, w.rh, fmaf(-x.y, w.ih, lr)), fmaf(x.x, w.ih, fmaf(x.y, w.rh, li))};
+    }
+    // the same product as mul, in packed FP32x2 instructions (bit-identical results)
+    static __device__ __forceinline__ cpx<float> mul2(cpx<float> x, C w)
+    {
+        const float2 xx = make_float2(x.x, x.x), yy = make_float2(-x.y, x.y);
+        const float2 l = __ffma2_rn(xx, make_float2(w.rl, w.il), __fmul2_rn(yy, make_float2(w.il, w.rl)));
+        const float2 r = __ffma2_rn(xx, make_float2(w.rh, w.ih), __ffma2_rn(yy, make_float2(w.ih, w.rh), l));
+        return {r.x, r.y};
     }
     static __device__ __forceinline__ C conj(C w) { return {w.rh, -w.ih, w.rl, -w.il}; }
     static __device__ __forceinline__ cpx<float> mulr(cpx<float> x, Rl s)
@@ -128,12 +155,13 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ S conj_s(S w) { return {w.x, -w.y}; }
 };
 
-// a * (rh + i ih) with the constant's low parts (rl, il) in FP32; plain product in FP64
-template <typename T> __device__ __forceinline__ cpx<T> mulk(cpx<T> a, double re, double im)
+// a * (rh + i ih) with the constant's low parts (rl, il) in FP32 (PK: the packed product); plain
+// product in FP64
+template <typename T, bool PK = false> __device__ __forceinline__ cpx<T> mulk(cpx<T> a, double re, double im)
 {
     if constexpr (sizeof(T) == 4) {
-        return Prec<float>::mul(a, Prec<float>::C{(float)re, (float)im, (float)(re - (double)(float)re),
-                                                  (float)(im - (double)(float)im)});
+        const Prec<float>::C w{(float)re, (float)im, (float)(re - (double)(float)re), (float)(im - (double)(float)im)};
+        return PK ? Prec<float>::mul2(a, w) : Prec<float>::mul(a, w);
     } else {
         return a * mk<T>(re, im);
     }
@@ -199,26 +227,26 @@ __device__ __forceinline__ Draws draws(unsigned long long seed, uint32_t k)
 // ------------------------------------------------------------------------------------------------
 // x * exp(-2 pi i j/16) for a compile-time j (after unrolling the switch folds away); the constants
 // cos(pi/8), sin(pi/8), sqrt(1/2) enter with their FP32 low parts in the FP32 form
-template <typename T> __device__ __forceinline__ cpx<T> tw16(cpx<T> a, int j)
+template <typename T, bool PK = false> __device__ __forceinline__ cpx<T> tw16(cpx<T> a, int j)
 {
     constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173, h = 0.70710678118654752440;
     switch (j & 15) {
     case 0: return a;
-    case 1: return mulk(a, c1, -s1);
+    case 1: return mulk<T, PK>(a, c1, -s1);
     case 2: return mk(mulkr<T>(a.x + a.y, h), mulkr<T>(a.y - a.x, h));
-    case 3: return mulk(a, s1, -c1);
+    case 3: return mulk<T, PK>(a, s1, -c1);
     case 4: return mul_mi(a);
-    case 5: return mulk(a, -s1, -c1);
+    case 5: return mulk<T, PK>(a, -s1, -c1);
     case 6: return mk(mulkr<T>(a.y - a.x, h), mulkr<T>(-a.x - a.y, h));
-    case 7: return mulk(a, -c1, -s1);
+    case 7: return mulk<T, PK>(a, -c1, -s1);
     case 8: return mk(-a.x, -a.y);
-    case 9: return mulk(a, -c1, s1);
+    case 9: return mulk<T, PK>(a, -c1, s1);
     case 10: return mk(mulkr<T>(-a.x - a.y, h), mulkr<T>(a.x - a.y, h));
-    case 11: return mulk(a, -s1, c1);
+    case 11: return mulk<T, PK>(a, -s1, c1);
     case 12: return mul_i(a);
-    case 13: return mulk(a, s1, c1);
+    case 13: return mulk<T, PK>(a, s1, c1);
     case 14: return mk(mulkr<T>(a.x - a.y, h), mulkr<T>(a.x + a.y, h));
-    default: return mulk(a, c1, s1);
+    default: return mulk<T, PK>(a, c1, s1);
     }
 }
 
