@@ -359,6 +359,53 @@ template <> struct Dyn<float> {
         *fi = s * mag;
         *e = em1;
     }
+    // both points of a pair at once in packed FP32x2 instructions, the same operations per component
+    // as f1t / em1 (bit-identical); a pair with a point outside the series' range takes f1t per point
+    static __device__ __forceinline__ void f1t2(float2 a, float2 t, float2 *fr, float2 *fi, float2 *e)
+    {
+        if (a.x >= -0.5f && a.y >= -0.5f && fabsf(t.x) <= 1.0f && fabsf(t.y) <= 1.0f) {
+            float2 p = __ffma2_rn(make_float2(1.0f / 40320.0f, 1.0f / 40320.0f), a, make_float2(1.0f / 5040.0f, 1.0f / 5040.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 720.0f, 1.0f / 720.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 120.0f, 1.0f / 120.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+            p = __ffma2_rn(p, a, make_float2(0.5f, 0.5f));
+            p = __ffma2_rn(p, a, make_float2(1.0f, 1.0f));
+            const float2 em1 = __fmul2_rn(a, p);
+            const float2 u = __fmul2_rn(t, t);
+            float2 ps = __ffma2_rn(make_float2(1.0f / 362880.0f, 1.0f / 362880.0f), u, make_float2(-1.0f / 5040.0f, -1.0f / 5040.0f));
+            ps = __ffma2_rn(ps, u, make_float2(1.0f / 120.0f, 1.0f / 120.0f));
+            ps = __ffma2_rn(ps, u, make_float2(-1.0f / 6.0f, -1.0f / 6.0f));
+            ps = __ffma2_rn(ps, u, make_float2(1.0f, 1.0f));
+            const float2 s = __fmul2_rn(t, ps);
+            float2 pc = __ffma2_rn(make_float2(-1.0f / 3628800.0f, -1.0f / 3628800.0f), u, make_float2(1.0f / 40320.0f, 1.0f / 40320.0f));
+            pc = __ffma2_rn(pc, u, make_float2(-1.0f / 720.0f, -1.0f / 720.0f));
+            pc = __ffma2_rn(pc, u, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+            pc = __ffma2_rn(pc, u, make_float2(-0.5f, -0.5f));
+            const float2 cm1 = __fmul2_rn(u, pc);
+            const float2 mag = __fadd2_rn(make_float2(1.0f, 1.0f), em1);
+            *fr = __ffma2_rn(cm1, mag, em1);
+            *fi = __fmul2_rn(s, mag);
+            *e = em1;
+        } else {
+            f1t(a.x, t.x, &fr->x, &fi->x, &e->x);
+            f1t(a.y, t.y, &fr->y, &fi->y, &e->y);
+        }
+    }
+    static __device__ __forceinline__ float2 em1_2(float2 a)
+    {
+        if (a.x >= -0.5f && a.y >= -0.5f) {
+            float2 p = __ffma2_rn(make_float2(1.0f / 40320.0f, 1.0f / 40320.0f), a, make_float2(1.0f / 5040.0f, 1.0f / 5040.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 720.0f, 1.0f / 720.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 120.0f, 1.0f / 120.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+            p = __ffma2_rn(p, a, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+            p = __ffma2_rn(p, a, make_float2(0.5f, 0.5f));
+            p = __ffma2_rn(p, a, make_float2(1.0f, 1.0f));
+            return __fmul2_rn(a, p);
+        }
+        return make_float2(em1(a.x), em1(a.y));
+    }
 };
 template <> struct Dyn<double> {
     static __device__ __forceinline__ void f1(double a, double y, double *fr, double *fi, double *e)
@@ -736,6 +783,7 @@ template <typename T, int N, int V> struct Fused {
 // ------------------------------------------------------------------------------------------------
 template <typename T, int N, int V> struct Pointwise {
     using K = Fused<T, N, V>;
+    static constexpr bool PD = sizeof(T) == 4 && N >= 2048 && N <= 8192;
     using PR = Prec<T>;
     using C = typename Prec<T>::C;
     static constexpr int G = K::G;
@@ -819,6 +867,21 @@ template <typename T, int N, int V> struct Pointwise {
         const T Bpi = (T)3.14159265358979323846 * B;   // the phase coefficient: t = pi B j^2
 #pragma unroll 2
         for (int k = g; k < N / 2; k += G) {
+            // FP32 at N = 2048 .. 8192: the series of the pair (2k, 2k+1) in packed FP32x2 instructions
+            // (bit-identical; +1.6% / +2.4% / +0.7% at N = 2048 / 4096 / 8192, -0.9% at 1024 and 16384)
+            float2 F1R, F1I = make_float2(0.f, 0.f), EM1, Z;
+            if constexpr (PD) {
+                const float j0 = (float)(2 * k), j1 = (float)(2 * k + 1);
+                const float2 j2 = __fmul2_rn(make_float2(j0, j1), make_float2(j0, j1));
+                const float2 a2 = __fmul2_rn(make_float2(A, A), j2);
+                if (phase) {
+                    Dyn<float>::f1t2(a2, __fmul2_rn(make_float2(Bpi, Bpi), j2), &F1R, &F1I, &EM1);
+                } else {
+                    EM1 = Dyn<float>::em1_2(a2);
+                    F1R = EM1;
+                }
+                Z = __fmul2_rn(make_float2(D, D), j2);
+            }
 #pragma unroll
             for (int par = 0; par < 2; ++par) {
                 const int j = 2 * k + par;
@@ -830,7 +893,12 @@ template <typename T, int N, int V> struct Pointwise {
                 // identically every step and add up)
                 T f1r, f1i = (T)0, em1;
                 T z = (T)0;
-                if constexpr (sizeof(T) == 4) {
+                if constexpr (PD) {
+                    f1r = par ? F1R.y : F1R.x;
+                    f1i = par ? F1I.y : F1I.x;
+                    em1 = par ? EM1.y : EM1.x;
+                    z = par ? Z.y : Z.x;
+                } else if constexpr (sizeof(T) == 4) {
                     // j^2 is exact in FP32 up to N = 4096 (and rounded once above); the coefficients
                     // change every step, so no rounding of a, t or z repeats from step to step
                     const T j2 = fj * fj;
