@@ -44,8 +44,8 @@ N_GRID, L_BOX, DT = 4096, 40.0, 0.001
 # (608 trajectories through 300 and through 1000 steps; dram__bytes_read.sum + dram__bytes_write.sum):
 # a launch costs a fixed part (the first touch of the tables) plus a part per trajectory-step (the
 # per-step tables that fall out of L2).  None until the kernel has been captured again after a change.
-PROFILED_DRAM_FIXED_BYTES = 1.256e6
-PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 2.22
+PROFILED_DRAM_FIXED_BYTES = 1.107e6
+PROFILED_DRAM_BYTES_PER_TRAJ_STEP = 2.63
 N_STEPS_FULL = 11899          # ceil((tau_f - tau0) / (hbar c dt)) for the Bjorken medium 0.425 -> 0.25 GeV at tau0 = 0.6 fm/c
 
 
