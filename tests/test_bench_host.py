@@ -1,11 +1,14 @@
 """Host-side arithmetic of bench.py: the flop counts behind the roofline figures, the FP32 peak
 from unit counts, the parsing of the clock samples taken during the timed region, and the
 reference arm's JSON line (with the oracle sample replaced by a stand-in, so that no oracle work
-runs here)."""
+runs here); the precision study's medium step count against the oracle's, and the DFT16 study's
+column count."""
 import importlib.util
 import json
 import os
 from types import SimpleNamespace
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -88,3 +91,24 @@ def test_reference_arm_line(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     b.run_reference(SimpleNamespace(steps=1, warmup=0, gpus=2))
     assert capsys.readouterr().out == ""
+
+
+def test_precision_study_step_count_matches_oracle():
+    """precision.medium_step_count (the error model's step count for rMin-shortcut records) agrees
+    with the oracle's own step count for Bjorken media, including the two workloads' 11,899 and 23,797."""
+    import oracle as o
+    from paper_2107_06147_gb300 import precision
+    assert precision.medium_step_count(0.425, 0.6, 0.25, 0.001) == 11899
+    assert precision.medium_step_count(0.425, 0.6, 0.25, 0.0005) == 23797
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        T0 = float(rng.uniform(0.3, 0.6)); Tf = T0 * float(rng.uniform(0.4, 0.95)); dt = float(rng.choice([0.001, 0.0005]))
+        g = o.Grid(N=64, L=5.0, dt=dt)
+        assert precision.medium_step_count(T0, 0.6, Tf, dt) == o.n_steps(g, o.medium(T0, 0.6, Tf, 5.0, 0.0))
+
+
+def test_dft16_study_column_count():
+    """A trajectory-step runs 2 transforms x log16(N) radix-16 passes x N/16 columns."""
+    from paper_2107_06147_gb300 import tcstudy
+    assert tcstudy.columns_per_traj_step(4096) == 2 * 3 * 256
+    assert tcstudy.columns_per_traj_step(65536) == 2 * 4 * 4096
